@@ -1,0 +1,363 @@
+"""Benchmark of the fused PageRank hot path on GB300.
+
+Workload (one step): on a device-resident R-MAT scale-22 edge list (edge
+factor 16, a/b/c/d = 0.57/0.19/0.19/0.05, self-loops and duplicates removed,
+exactly 10% of vertices dangling, seed 1), build the graph on the device and
+solve PageRank (d = 0.85) to L1 successive difference / FP64 residual
+<= 1e-10 with both sweeps: Jacobi (Algorithm 1) and the fused sweep
+(Algorithm 2), in the chosen precision (default FP32 sweep with FP64 defect
+correction).  The 268 MB index stream of each sweep exceeds the 126 MB L2, so
+no explicit flush is needed between steps.
+
+value = edges traversed per second over the whole step (GTEPS): the sum over
+both solves of E x sweeps (inner and FP64 residual sweeps), divided by the
+step time, build included.  The JSON line also carries the time to solution
+of each solve, the plain FP64 solves for comparison, the roofline of the
+sweep kernel, an oracle CPU baseline and an end-to-end figure with host
+buffers.
+
+--impl reference times the CPU oracle (plain single-threaded FP64) on the same
+graph: each step is a bounded sample (a few Jacobi and fused sweeps).
+Multi-GPU: the workload does not shard (one graph); --gpus N runs N
+independent replicas (weak scaling), one per rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "R-MAT-22 time to L1<1e-10 and GTEPS (% HBM peak), mixed/fused vs plain FP64"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx = max(mx, float(p[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(scale):
+    import gen
+    return gen.rmat(scale, 16, seed=1, dangling_frac=0.10)
+
+
+def b_alg(n, m, prec):
+    """Algorithmic bytes of one sweep: index stream 4E, offsets 4(n+1), the
+    gathered vector once (s_g n) and the rank read and write (2 s_x n)."""
+    s = {"fp64": 8, "fp32": 4, "fp32_dc": 4, "bf16_dc": 2, "fp16_dc": 2}[prec]
+    return 4 * m + 4 * (n + 1) + 3 * s * n
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2203_09284_gb300 as fp
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    n, src_h, dst_h = workload(args.scale)
+    m = len(src_h)
+    src = torch.from_numpy(src_h).to(dev)
+    dst = torch.from_numpy(dst_h).to(dev)
+    precs = [args.precision]
+    variants = ["jacobi", "gs"]
+
+    def step(prec, x_out):
+        g = fp.Graph(n, src, dst)
+        res = []
+        for i, v in enumerate(variants):
+            _, r = g.solve(out=x_out[i], variant=v, precision=prec, threshold=1e-10,
+                           max_iter=1000)
+            res.append(r)
+        g.close()
+        return res
+
+    x_out = [torch.empty(n, dtype=torch.float64, device=dev) for _ in variants]
+    # warm-up (also instantiates graphs, allocator pools)
+    for _ in range(args.warmup):
+        res = step(args.precision, x_out)
+    torch.cuda.synchronize()
+    launches0 = fp.kernel_launches()
+
+    # ---- timed region: K steps, events on the launching stream ----------
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(dev.index) as clk:
+        ev0.record(stream)
+        all_res = []
+        for _ in range(args.steps):
+            all_res.append(step(args.precision, x_out))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    launches = fp.kernel_launches() - launches0
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_step = float(t.item()) / args.steps
+    sweeps = sum(r.iters + r.outer_iters for r in all_res[-1])
+    value = world * m * sweeps / (ms_step * 1e-3) / 1e9
+
+    # ---- breakdown (outside the timed region) ----------------------------
+    def timed(fn, reps=3):
+        best = None
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            out = fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            t_ = a.elapsed_time(b)
+            best = t_ if best is None or t_ < best else best
+        return best, out
+
+    build_ms, g = timed(lambda: fp.Graph(n, src, dst))
+    solves = {}
+    for prec in dict.fromkeys([args.precision, "fp64"]):
+        for v in variants:
+            ms, (x, r) = timed(lambda: g.solve(out=x_out[0], variant=v, precision=prec,
+                                               threshold=1e-10, max_iter=1000))
+            solves[f"{v}_{prec}"] = {"ms": round(ms, 4), "iters": r.iters,
+                                     "outer": r.outer_iters, "residual": r.residual,
+                                     "gteps": round(m * (r.iters + r.outer_iters) / ms / 1e6, 2)}
+
+    # dominant kernel: the cheap sweep of the headline precision, timed by
+    # events around back-to-back launches of the device loop
+    sweep_prec = {"fp32_dc": "fp32", "bf16_dc": "fp32", "fp16_dc": "fp32"}.get(args.precision,
+                                                                             args.precision)
+    k_long, k_short = 41, 1
+    t_long, _ = timed(lambda: g.solve(out=x_out[0], variant="jacobi", precision=sweep_prec,
+                                      threshold=0.0, max_iter=k_long))
+    t_short, _ = timed(lambda: g.solve(out=x_out[0], variant="jacobi", precision=sweep_prec,
+                                       threshold=0.0, max_iter=k_short))
+    sweep_ms = (t_long - t_short) / (k_long - k_short)
+    alg = b_alg(n, m, sweep_prec)
+    peaks = _peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = alg / (sweep_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                "kernel": f"k_sweep<{sweep_prec}, jacobi>", "sweep_us": round(sweep_ms * 1e3, 2),
+                "alg_bytes_per_sweep": alg, "peak_source": peak_src}
+
+    # ---- end to end through the public API with host buffers --------------
+    src_pin = torch.from_numpy(src_h).pin_memory()
+    dst_pin = torch.from_numpy(dst_h).pin_memory()
+    x_host = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in variants]
+
+    def e2e_step():
+        s_d = src_pin.to(dev, non_blocking=True)
+        d_d = dst_pin.to(dev, non_blocking=True)
+        gg = fp.Graph(n, s_d, d_d)
+        tot = 0
+        for i, v in enumerate(variants):
+            _, r = gg.solve(out=x_out[i], variant=v, precision=args.precision, threshold=1e-10)
+            x_host[i].copy_(x_out[i], non_blocking=True)
+            tot += r.iters + r.outer_iters
+        gg.close()
+        return tot
+
+    e2e_step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    tot = 0
+    for _ in range(args.steps):
+        tot += e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / args.steps
+    e2e = {"value": round(world * m * (tot / args.steps) / (e2e_ms * 1e-3) / 1e9, 3),
+           "unit": "GTEPS", "h2d_bytes_per_step": 8 * m,
+           "d2h_bytes_per_step": 8 * n * len(variants), "ms_per_step": round(e2e_ms, 3)}
+    g.close()
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GTEPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "fp32_dc": "f32+f64", "bf16_dc": "bf16+f32+f64",
+                  "fp16_dc": "f16+f32+f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"rmat{args.scale}_ef16_dangling10_seed1", "n": n, "edges": m,
+                   "precision": args.precision, "variants": variants, "d": 0.85,
+                   "threshold": 1e-10, "step": "device build + jacobi solve + fused solve",
+                   "l2_flush": "inputs larger than L2 (index stream 4E per sweep)",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "time_to_solution_ms": {k: v["ms"] for k, v in solves.items()},
+        "solves": solves, "build_ms": round(build_ms, 3),
+        "gpu_launches": int(launches),
+        "roofline": roofline, "e2e": e2e, "clocks": clk.summary(),
+    }
+    return out
+
+
+def cpu_baseline(scale, budget_s=15.0):
+    """The oracle (single-threaded FP64) on a bounded sample of the workload."""
+    import oracle
+    n, src, dst = workload(scale)
+    m = len(src)
+    t0 = time.perf_counter()
+    g = oracle.build_graph(n, src, dst)
+    t_build = time.perf_counter() - t0
+    sweeps, t = 0, 0.0
+    x0 = None
+    while t < budget_s and sweeps < 40:
+        t1 = time.perf_counter()
+        oracle.jacobi(g, 0.85, tau=-1, max_iter=2, normalize=False, x0=x0)
+        oracle.gauss_seidel(g, 0.85, tau=-1, max_iter=2, normalize=False, x0=x0)
+        t += time.perf_counter() - t1
+        sweeps += 4
+    return {"value": round(m * sweeps / t / 1e9, 4), "unit": "GTEPS", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{sweeps} FP64 sweeps (half Jacobi, half fused) of the R-MAT-{scale} "
+                      f"graph after an oracle build of {t_build:.1f} s; single thread"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--precision", default="fp32_dc",
+                    choices=["fp64", "fp32", "fp32_dc", "bf16_dc", "fp16_dc"])
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per sweep launch from an ncu capture (reported as is)")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+
+    if args.impl == "reference":
+        if rank == 0:
+            line = reference_arm(args)
+            print(json.dumps(line))
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(args.scale)
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+def reference_arm(args):
+    """The oracle timed as it stands, on the host cores, on bounded samples."""
+    import oracle
+    n, src, dst = workload(args.scale)
+    m = len(src)
+    g = oracle.build_graph(n, src, dst)
+    per_step = 2  # sweeps of each variant per step
+    for _ in range(args.warmup):
+        oracle.jacobi(g, 0.85, tau=-1, max_iter=1, normalize=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.jacobi(g, 0.85, tau=-1, max_iter=per_step, normalize=False)
+        oracle.gauss_seidel(g, 0.85, tau=-1, max_iter=per_step, normalize=False)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = m * 2 * per_step / dt / 1e9
+    sample = (f"{2 * per_step} FP64 sweeps ({per_step} Jacobi + {per_step} fused) of the "
+              f"R-MAT-{args.scale} graph per step, single thread")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GTEPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"rmat{args.scale}_ef16_dangling10_seed1", "n": n,
+                       "edges": m, "precision": args.precision},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * fusedpr.h -- C ABI of the GB300 fused PageRank library (libfusedpr.so).
+ *
+ * Problem (the paper's Sec. 3 and Eq. 1): a directed graph G(V, E) given as a
+ * list of (u, v) tuples, each an out-link of u and an in-link of v; the
+ * PageRank vector solves
+ *     pr_u = (1-d)/n + d * ( sum_{v in inlink(u)} pr_v / d_o(v) + D/n ),
+ * where D is the rank held by dangling vertices (out-degree 0), spread
+ * uniformly (the paper's Eq. 1 has no dangling term; this library adds the
+ * uniform redistribution and normalises the result to sum 1).  Two sweeps:
+ *   PR_JACOBI    Algorithm 1 / Eq. 2: every vertex reads the previous sweep.
+ *   PR_FUSED_GS  Algorithm 2 / Eq. 9 (FusEd-PageRank): a vertex's new
+ *                contribution is written immediately and later readers in the
+ *                same sweep may see it (asynchronous Gauss-Seidel, as the
+ *                paper's parallel version).  Each sweep is followed by a
+ *                rescale to sum 1, folded into the next sweep as a scalar.
+ * Stop rule (Algorithm 1/2 `while error > threshold`, Eq. 3): the L1 (or
+ * max) distance between successive iterates; a sweep whose error is <= the
+ * threshold ends the solve.
+ *
+ * Conventions for every call:
+ *   - Pointers documented "device" are CUDA device pointers on the current
+ *     device; "host" pointers are ordinary host memory.  Inputs are only read
+ *     and stay owned by the caller; outputs are caller-allocated.
+ *   - All device work is ordered on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream).  Calls return after their result scalars are on the
+ *     host (one stream synchronisation), so device outputs are complete too.
+ *   - Every call returns a pr_status; nothing aborts or traps.  Device-side
+ *     errors (bad vertex ids, timeouts) come back through status words.
+ *     pr_last_error() gives a readable message for the calling thread.
+ *   - Indices are int32 (n < 2^31); edge counts are int64 but must be
+ *     < 2^31 (offsets are int32).
+ *   - There is no CPU fallback: without a usable CUDA device every call
+ *     returns PR_ERR_CUDA.
+ */
+#ifndef FUSEDPR_H
+#define FUSEDPR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pr_graph pr_graph; /* opaque; owns its device buffers */
+
+typedef enum {
+    PR_OK = 0,
+    PR_ERR_INVALID_ARG = 1, /* bad argument or vertex id (device-checked) */
+    PR_ERR_OOM = 2,         /* allocation failed (allocator or CUDA) */
+    PR_ERR_CUDA = 3,        /* CUDA runtime error; see pr_last_error() */
+    PR_NOT_CONVERGED = 4,   /* max_iter reached; outputs hold the last iterate */
+    PR_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    PR_ERR_UNSUPPORTED = 6  /* option combination not implemented */
+} pr_status;
+
+typedef enum { PR_JACOBI = 0, PR_FUSED_GS = 1 } pr_variant;
+
+/* Arithmetic of the sweep.  *_DC forms run the cheap sweep on a correction
+ * and recompute the residual in FP64 between inner solves (defect
+ * correction); the stop value is then the FP64 residual
+ * || (1-d)/n + d M x - x ||_1.  BF16/FP16 store the gathered vector scaled by
+ * a power of two (n for the rank itself) with FP32 accumulation. */
+typedef enum {
+    PR_FP64 = 0,
+    PR_FP32 = 1,
+    PR_FP32_DC = 2,
+    PR_BF16_DC = 3,
+    PR_FP16_DC = 4
+} pr_precision;
+
+typedef enum { PR_NORM_L1 = 0, PR_NORM_LINF = 1 } pr_norm;
+
+/* Device allocator hooks (e.g. a framework's caching allocator).  alloc
+ * returns a device pointer of at least `bytes` usable on `stream`, or NULL;
+ * free releases it.  When the pr_allocator pointer passed to
+ * pr_graph_create is NULL the library uses cudaMallocAsync/cudaFreeAsync. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
+    void *ctx;
+} pr_allocator;
+
+/* Launch parameters of the sweep (chosen by the autotuner; zero fields take
+ * the library defaults). */
+typedef struct {
+    int32_t t_lo;      /* in-degree <= t_lo: thread per vertex (default 8) */
+    int32_t t_hub;     /* in-degree >  t_hub: block per vertex, split in
+                          segments of hub_seg edges (default 2048) */
+    int32_t hub_seg;   /* edges per hub segment (default 8192) */
+    int32_t low_rounds;/* vertices per thread in a low-degree chunk (default 4) */
+    int32_t mid_per_warp; /* mid vertices per warp in a mid chunk (default 4) */
+    int32_t deterministic_gs; /* 1: fused sweep in strict id order on one CTA
+                                 (reproduces Eq. 9 exactly; n <= 65536) */
+} pr_tune;
+
+typedef struct {
+    double d;               /* damping factor, 0 <= d < 1 (paper: 0.85) */
+    double threshold;       /* stop when the sweep error <= threshold */
+    int32_t max_iter;       /* >= 1; sweeps (inner sweeps for *_DC) */
+    pr_variant variant;
+    pr_precision precision;
+    pr_norm norm;           /* error of a sweep: L1 or max norm (Eq. 3) */
+    const double *x0;       /* device [n] start vector (sum 1) or NULL: 1/n */
+    double *history;        /* device [max_iter] per-sweep error or NULL */
+    int32_t use_graph;      /* 1 (default): CUDA-graph loop with the stop test
+                               on the device; 0: host-driven loop */
+    int32_t max_outer;      /* *_DC: max FP64 residual evaluations (default 8) */
+    double inner_rel;       /* *_DC: inner stop, relative to ||r||_1 (0: auto) */
+    const pr_tune *tune;    /* NULL: the graph's defaults */
+} pr_options;
+
+typedef struct {
+    int32_t iters;          /* sweeps run (all inner sweeps for *_DC) */
+    int32_t outer_iters;    /* FP64 residual evaluations (*_DC), else 0 */
+    double residual;        /* final stop value */
+    double sum_before_norm; /* sum of the iterate before the final x /= sum */
+    pr_status status;
+} pr_result;
+
+/* Fills `o` with the defaults: d 0.85, threshold 1e-10, max_iter 1000,
+ * Jacobi, FP64, L1, no x0/history, CUDA-graph loop. */
+pr_status pr_options_default(pr_options *o);
+
+/*
+ * Builds the graph on the device from an edge list (Sec. 3 storage):
+ * out/in-degree histograms, the in-lists (CSC: column u = sources of u's
+ * in-edges, ascending, ties by input position), inverse out-degrees
+ * (IEEE 1.0/deg, 0 for dangling), in-degree bins and sweep work items.
+ *   n       vertices, >= 1
+ *   m       edges, 0 <= m < 2^31
+ *   src,dst device int32 [m]; ids must lie in [0, n) (checked on the
+ *           device: PR_ERR_INVALID_ARG otherwise).  Self-loops and repeated
+ *           edges are kept as ordinary edges.
+ *   w       device float [m] raw positive edge weights, or NULL (unweighted).
+ *           Weighted graphs use P_uv = w_uv / sum_v' w_uv'.
+ *   flags   PR_BUILD_CSR also builds the out-lists (needed by pr_backward;
+ *           built lazily otherwise).
+ *   alloc   allocator hooks or NULL (cudaMallocAsync); kept by the graph.
+ *   out     receives the handle (NULL on error).
+ */
+#define PR_BUILD_CSR 1u
+pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                          const float *w, uint32_t flags, const pr_allocator *alloc,
+                          void *stream, pr_graph **out);
+
+/* Releases the graph and its buffers (NULL is ignored). */
+void pr_graph_destroy(pr_graph *g);
+
+/* Host outputs (each nullable): vertex and edge counts, dangling vertices,
+ * and the sizes of the low/mid/hub in-degree bins. */
+pr_status pr_graph_info(const pr_graph *g, int32_t *n, int64_t *m, int32_t *n_dangling,
+                        int32_t *bin_counts3);
+
+/*
+ * Copies the build products to caller device buffers (each nullable), for
+ * bit-exact checks: outdeg/indeg [n], col_ptr/row_ptr [n+1], row_idx/csc_eid
+ * [m] (in-lists), col_idx/csr_eid [m] (out-lists, ordered by (dst, input
+ * position); built on demand), inv_outdeg [n] (FP64), bins [n] (low, then
+ * mid, then hub vertex ids, each ascending).
+ */
+pr_status pr_graph_export(pr_graph *g, int32_t *outdeg, int32_t *indeg, int32_t *col_ptr,
+                          int32_t *row_idx, int32_t *csc_eid, int32_t *row_ptr,
+                          int32_t *col_idx, int32_t *csr_eid, double *inv_outdeg,
+                          int32_t *bins, void *stream);
+
+/*
+ * Solves for the PageRank vector.
+ *   x_out  device double [n]: the result, normalised to sum 1.
+ *   res    host, nullable: sweeps, stop value, status.
+ * Returns PR_OK, PR_NOT_CONVERGED (x_out holds the last iterate,
+ * normalised), or an error.
+ */
+pr_status pr_solve(pr_graph *g, const pr_options *o, double *x_out, pr_result *res,
+                   void *stream);
+
+/*
+ * Personalised PageRank for B teleport vectors at once (multi right-hand
+ * side sweep): column b teleports to the single vertex seeds[b] and its
+ * dangling mass is redistributed to the same vertex.  FP32 sweep
+ * (o->precision must be PR_FP32); each column stops on its own L1 error.
+ *   seeds  device int32 [B], ids in [0, n)
+ *   X_out  device float [n][B] (vertex-major, column b at stride B),
+ *          each column normalised to sum 1
+ *   res    host [B], nullable
+ */
+pr_status pr_solve_batched(pr_graph *g, const pr_options *o, int32_t B, const int32_t *seeds,
+                           float *X_out, pr_result *res, void *stream);
+
+/*
+ * Solves G independent graphs in one sequence of launches (each sweep is one
+ * kernel over the work items of every graph that has not converged yet).
+ *   graphs  host [G] handles (distinct)
+ *   x_out   host [G] array of device double pointers, x_out[i] of size n_i
+ *   res     host [G], nullable
+ * o->variant must be PR_JACOBI and o->precision PR_FP64 or PR_FP32.
+ */
+pr_status pr_solve_multi(pr_graph *const *graphs, int32_t G, const pr_options *o,
+                         double *const *x_out, pr_result *res, void *stream);
+
+/*
+ * Reverse mode of pr_solve at its fixed point.  Given x (the forward result)
+ * and grad_x = dL/dx, solves the transposed system
+ *     (I - d M)^T lambda = grad_x
+ * by iteration over the out-lists, then
+ *     dL/dw_e = (d x_u / s_u) (lambda_v - sum_v' P_uv' lambda_v')  for e = u->v
+ *     dL/dd   = lambda^T (M x - 1/n)
+ * (raw weights w with row sums s_u; unweighted graphs use w = 1).
+ *   x, grad_x  device double [n]
+ *   grad_w     device double [m] in input edge order, or NULL
+ *   grad_d     device double [1], or NULL
+ * o->threshold applies to the L1 change of lambda per sweep.
+ */
+pr_status pr_backward(pr_graph *g, const pr_options *o, const double *x, const double *grad_x,
+                      double *grad_w, double *grad_d, pr_result *res, void *stream);
+
+/* Static string for a status code. */
+const char *pr_status_string(pr_status s);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char *pr_last_error(void);
+
+/* Number of CUDA kernels the library has launched in this process so far
+ * (each iteration of a device-side loop counts as one launch).  Diagnostics
+ * only; no device work. */
+uint64_t pr_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FUSEDPR_H */

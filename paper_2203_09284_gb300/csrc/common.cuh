@@ -1,0 +1,213 @@
+// common.cuh -- internal declarations shared by the CUDA translation units of
+// libfusedpr: the graph handle, device allocation through the caller's hooks,
+// error reporting and small device helpers.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/fusedpr.h"
+
+namespace fpr {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------- errors --
+void set_error(const char *fmt, ...);
+// process-wide count of kernel launches issued by the library (diagnostics)
+void note_launch(unsigned long long k = 1);
+unsigned long long launches();
+pr_status cuda_status(cudaError_t e, const char *what, const char *file, int line);
+
+#define PR_CUDA(expr)                                                                    \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess) return ::fpr::cuda_status(_e, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+#define PR_TRY(expr)                          \
+    do {                                              \
+        pr_status _s = (expr);                        \
+        if (_s != PR_OK) return _s;                   \
+    } while (0)
+
+#define PR_LAUNCH_CHECK() PR_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------------ allocation --
+struct Mem {
+    pr_allocator hooks{};
+    bool has_hooks = false;
+    cudaStream_t stream = nullptr;  // stream of the owner (used at destroy)
+    void *alloc(size_t bytes, cudaStream_t s);
+    void free(void *p, size_t bytes, cudaStream_t s);
+};
+
+// A device buffer owned by a graph (freed at destroy or on resize).
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+// Exact fixed-point accumulators of a sweep's partial sums (two words:
+// integer part scaled by 2^40, fraction scaled by 2^80).  Blocks add into
+// slot blockIdx % ACC_SLOTS so that same-address atomics do not serialise;
+// integer sums make the total independent of the slot and of the order.
+constexpr int ACC_SLOTS = 32;
+struct alignas(64) AccSlot {
+    long long res_hi, res_lo, dang_hi, dang_lo, sum_hi, sum_lo;
+    unsigned long long res_max;  // bit pattern of the largest |x' - x| (>= 0)
+    long long pad;
+};
+
+// Device state of one solve: scalars read by every block at the start of a
+// sweep and rewritten by the block that finishes the sweep last.
+struct SolveState {
+    AccSlot acc[ACC_SLOTS];      // reset by the finishing block
+    unsigned int ticket;         // blocks finished in this sweep
+    int iter;                    // sweeps completed
+    int done;                    // 1: stop (converged or out of sweeps)
+    int status;                  // PR_OK / PR_NOT_CONVERGED / error
+    int norm;
+    int max_iter;
+    int record;                  // history != nullptr
+    int phase;                   // defect correction: 0 inner sweeps, 1 outer step
+    int inner_iter;              // defect correction: sweeps in this inner solve
+    int outer_iter;              // defect correction: residual evaluations
+    int max_outer;
+    int pad0;
+    double tau;
+    double d;
+    double base;      // (1-d)/n
+    double inv_n;     // 1/n
+    double dang;      // dangling mass of the current iterate (stored units)
+    double sigma;     // true value = sigma * stored value (fused sweep rescale)
+    double res;       // last sweep's L1 error (true units)
+    double resmax;    // last sweep's max error
+    double sum;       // sum of the current iterate (stored units)
+    double scale;     // defect correction: power-of-two scale of the correction
+    double rnorm;     // defect correction: ||r||_1 of the current outer step
+    double inner_tol; // defect correction: inner stop threshold (true units)
+    double inner_rel;
+    double mass_target; // fused defect correction: exact sum of the correction
+    double *history;
+};
+
+// Work decomposition of a sweep over the in-degree bins: a run of blocks per
+// bin role, in the order hub segments, mid chunks, low chunks.
+struct Items {
+    int32_t t_lo = -1, t_hub = -1, hub_seg = 0;
+    int32_t nlow = 0, nmid = 0, nhub = 0;
+    int32_t nhubseg = 0;          // blocks of the hub role
+    int32_t low_rounds = 4;       // vertices per thread in a low chunk
+    int32_t mid_per_warp = 4;     // vertices per warp in a mid chunk
+    Buf bins;                     // [n] low | mid | hub vertex ids
+    Buf hubseg_start;             // [nhub + 1] first segment of each hub
+    Buf seg_acc;                  // [nhubseg] double partial sums
+    Buf hub_cnt;                  // [nhub] segments finished this sweep
+    int32_t low_blocks(int bs) const {
+        int per = bs * low_rounds;
+        return (nlow + per - 1) / per;
+    }
+    int32_t mid_blocks(int bs) const {
+        int per = (bs / 32) * mid_per_warp;
+        return (nmid + per - 1) / per;
+    }
+};
+
+}  // namespace fpr
+
+// Opaque handle of the C ABI.
+struct pr_graph {
+    int device = 0;
+    int num_sms = 0;
+    int32_t n = 0;
+    int64_t m = 0;
+    int32_t n_dangling = 0;
+    fpr::Mem mem;
+    std::vector<fpr::Buf *> owned;
+
+    // build products
+    fpr::Buf outdeg, indeg, col_ptr, row_idx, csc_eid;
+    fpr::Buf row_ptr, col_idx, csr_eid;  // out-lists (lazy)
+    fpr::Buf inv64, inv32;               // 1/outdeg (0 for dangling)
+    fpr::Items items;
+    pr_tune tune{};
+
+    // weighted graphs: raw weights and row-normalised P per in-list slot
+    bool weighted = false;
+    fpr::Buf w, rowsum, p64_csc, p32_csc;
+
+    // solve workspace (grown on demand)
+    fpr::Buf ybuf;      // 2 x n x 8 bytes: stored vectors
+    fpr::Buf xbuf;      // n doubles: FP64 iterate for defect correction
+    fpr::Buf rbuf;      // n x 8 bytes: residual / right-hand side
+    fpr::Buf state;     // SolveState
+    fpr::Buf aux;       // scratch for batched / multi / adjoint
+    fpr::SolveState *host_state = nullptr;  // pinned mirror
+
+    // cached CUDA graphs of the solve loop
+    struct Cached {
+        int key = -1;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraph_t graph = nullptr;
+    };
+    std::vector<Cached> graphs;
+};
+
+namespace fpr {
+
+pr_status buf_alloc(pr_graph *g, Buf &b, size_t bytes, cudaStream_t s);
+void buf_free(pr_graph *g, Buf &b, cudaStream_t s);
+pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s);
+pr_status ensure_csr(pr_graph *g, cudaStream_t s);
+pr_tune effective_tune(const pr_graph *g, const pr_tune *t);
+void release_graphs(pr_graph *g);
+
+// exclusive scan of `count` int32 values; out[count] receives the total.
+pr_status scan_exclusive(pr_graph *g, const int32_t *in, int32_t *out, int64_t count,
+                         cudaStream_t s);
+
+// ------------------------------------------------------------ device side --
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+// Adds p (|p| < 2^20) into a two-word fixed-point accumulator: the integer
+// part of p * 2^40 and the remaining fraction scaled by a further 2^40
+// (truncated below 2^-80).  Integer addition is associative, so totals do not
+// depend on the order in which blocks finish; up to 2^23 terms fit.
+__device__ __forceinline__ void fx_add(long long *hi, long long *lo, double p)
+{
+    double t = p * 1099511627776.0;  // 2^40, exact
+    double h = floor(t);
+    double f = t - h;                // exact, in [0, 1)
+    atomicAdd(reinterpret_cast<unsigned long long *>(hi),
+              static_cast<unsigned long long>(static_cast<long long>(h)));
+    atomicAdd(reinterpret_cast<unsigned long long *>(lo),
+              static_cast<unsigned long long>(static_cast<long long>(f * 1099511627776.0)));
+}
+__device__ __forceinline__ double fx_value(long long hi, long long lo)
+{
+    return static_cast<double>(hi) * 9.094947017729282e-13 +   // 2^-40
+           static_cast<double>(lo) * 8.271806125530277e-25;    // 2^-80
+}
+
+}  // namespace fpr

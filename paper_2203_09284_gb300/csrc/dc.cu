@@ -1,0 +1,392 @@
+// dc.cu -- mixed precision with FP64 defect correction.
+//
+// The FP64 iterate x (stored in the contribution form Y64 with scale sigma_x)
+// is improved by corrections e that solve (I - d M) e = r, r = F(x) - x:
+//   outer step:  r = (1-d)/n + d M x - x    FP64 gather and arithmetic (the
+//                                           only FP64 sweep); stop if
+//                                           ||r||_1 <= threshold
+//   inner loop:  e <- r + d M e              the cheap sweep, e stored as
+//                                           FP32 / BF16 / FP16 times 2^k,
+//                                           FP32 accumulation; Jacobi or fused
+//   update:      x <- (x + e) / sum(x + e)   FP64
+// The three steps are nested WHILE loops of one CUDA graph: the residual
+// kernel decides whether another inner solve is needed, the last inner sweep
+// ends the inner loop, the update kernel ends the outer loop once the
+// residual kernel has declared convergence.
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "solve_impl.cuh"
+#include "sweep.cuh"
+
+namespace fpr {
+
+struct DCParams {
+    SweepParams p;           // traversal of the FP64 residual sweep (y0 = Y64)
+    float *r32;              // right-hand side of the correction solve
+    void *e0, *e1;           // correction buffers (stored form)
+    const float *inv32;
+    const double *inv64;
+    double *y64;
+    SolveState *sx, *se;     // outer and inner states
+    cudaGraphConditionalHandle h_inner, h_outer;
+    int use_cond;
+    int gs;                  // inner sweeps are fused (in place)
+    int fp16;                // scale the correction into the FP16 range
+};
+
+// Epilogue of the residual sweep: r_u in FP64, stored as FP32, and the first
+// correction iterate e = r written in the correction's stored form.
+template <typename Te>
+struct ResidFin {
+    const DCParams &q;
+    Ctx<double> c;
+    float rscale;  // 1 / sigma_e
+    Part<double> pt;
+    __device__ ResidFin(const DCParams &q_, const Ctx<double> &c_, float rs)
+        : q(q_), c(c_), rscale(rs) {}
+    __device__ __forceinline__ double operator()(int u, double acc)
+    {
+        const int od = q.p.outdeg[u];
+        const double yo = __ldg(q.y64 + u);
+        const double xold = od > 0 ? yo * static_cast<double>(od) : yo;
+        const double xnew = c.base + c.d * (c.sig * (acc + c.dt));
+        const double r = xnew - c.sig * xold;
+        const float rf = static_cast<float>(r);
+        q.r32[u] = rf;
+        const float es = rf * rscale;
+        static_cast<Te *>(q.e0)[u] = from_a<Te>(od > 0 ? es * q.inv32[u] : es);
+        const double ar = fabs(r);
+        pt.l1 += ar;
+        pt.lmax = ar > pt.lmax ? ar : pt.lmax;
+        pt.sm += es;
+        if (od == 0) pt.dm += es;
+        return xnew;
+    }
+};
+
+__device__ __forceinline__ double next_scale(const SolveState *sx, int fp16, double rnorm_pred,
+                                             double n)
+{
+    if (!fp16) return 1.0;
+    // correction entries average ||r||_1 / (n (1-d)); bring them near 1
+    double target = n * (1.0 - sx->d) / fmax(rnorm_pred, 1e-300);
+    int k = (int)lrint(log2(target));
+    k = max(-120, min(120, k));
+    return ldexp(1.0, -k);
+}
+
+template <typename Te>
+__global__ void __launch_bounds__(SWEEP_BS, 4) k_dc_resid(DCParams q)
+{
+    SolveState *sx = q.sx, *se = q.se;
+    if (sx->done) {
+        if (q.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(q.h_inner, 0u);
+        return;
+    }
+    ResidFin<Te> fin(q, load_ctx<double>(sx), static_cast<float>(1.0 / sx->scale));
+    run_items<double, double, false>(q.p, q.y64, fin);
+    block_partials<double>(sx, fin.pt);
+    if (!(last_block(sx) && threadIdx.x == 0)) return;
+    double res, resmax, dang_e, sum_e;
+    take_sums(sx, res, resmax, dang_e, sum_e);
+    sx->outer_iter += 1;
+    const int total = sx->iter + 1;
+    sx->iter = total;
+    sx->rnorm = res;
+    sx->res = res;
+    sx->resmax = resmax;
+    const double err = sx->norm ? resmax : res;
+    if (sx->history) sx->history[total - 1] = err;
+    const bool conv = err <= sx->tau;
+    bool go_on = !(conv || sx->outer_iter >= sx->max_outer || total >= sx->max_iter);
+    if (!go_on) {
+        sx->done = 1;
+        sx->status = conv ? PR_OK : PR_NOT_CONVERGED;
+        se->done = 1;
+    } else {
+        se->iter = 0;
+        se->done = 0;
+        se->dang = dang_e;
+        se->sum = sum_e;
+        se->sigma = sx->scale;
+        // inner stop on the L1 change of e (true units); the last outer step
+        // need not over-solve below the outer threshold
+        se->tau = fmax(sx->inner_rel * res, 0.05 * sx->tau);
+        se->norm = 0;
+    }
+    __threadfence();
+    if (q.use_cond) cudaGraphSetConditional(q.h_inner, go_on ? 1u : 0u);
+}
+
+// x <- x + e, renormalised through sigma_x; ends the outer loop when done.
+template <typename Te>
+__global__ void k_dc_update(DCParams q)
+{
+    SolveState *sx = q.sx, *se = q.se;
+    if (sx->done) {
+        if (q.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(q.h_outer, 0u);
+        return;
+    }
+    const Te *eb = static_cast<const Te *>((!q.gs && (se->iter & 1)) ? q.e1 : q.e0);
+    const double sgx = sx->sigma, sge = se->sigma;
+    Part<double> pt;
+    const int n = q.p.n;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const int od = q.p.outdeg[u];
+        const double yx = q.y64[u];
+        const double xs = od > 0 ? yx * static_cast<double>(od) : yx;
+        const float ev = to_a<float>(eb[u]);
+        const float es = od > 0 ? ev * static_cast<float>(od) : ev;
+        const double xn = sgx * xs + sge * static_cast<double>(es);
+        q.y64[u] = od > 0 ? xn * q.inv64[u] : xn;
+        pt.sm += xn;
+        if (od == 0) pt.dm += xn;
+    }
+    block_partials<double>(sx, pt);
+    if (!(last_block(sx) && threadIdx.x == 0)) return;
+    double res, resmax, dang, sum;
+    take_sums(sx, res, resmax, dang, sum);
+    sx->sum = sum;
+    sx->dang = dang;
+    sx->sigma = sum > 0 ? 1.0 / sum : 1.0;
+    // predicted size of the next residual: the inner solve's target
+    sx->scale = next_scale(sx, q.fp16, fmax(se->tau, sx->tau), (double)n);
+    __threadfence();
+    if (q.use_cond) cudaGraphSetConditional(q.h_outer, 1u);
+}
+
+__global__ void k_dc_first_scale(SolveState *sx, int fp16, double n)
+{
+    sx->scale = next_scale(sx, fp16, 1.0, n);
+}
+
+static double default_eta(pr_precision pr)
+{
+    switch (pr) {
+    case PR_FP32_DC: return 1e-6;
+    case PR_FP16_DC: return 4e-3;
+    case PR_BF16_DC: return 3e-2;
+    default: return 1e-6;
+    }
+}
+
+static int default_max_outer(pr_precision pr)
+{
+    switch (pr) {
+    case PR_FP32_DC: return 8;
+    case PR_FP16_DC: return 16;
+    case PR_BF16_DC: return 24;
+    default: return 8;
+    }
+}
+
+template <typename Te>
+static pr_status dc_graph(pr_graph *g, int key, DCParams &q, SweepParams &inner,
+                          unsigned grid_r, unsigned grid_s, unsigned grid_u,
+                          cudaGraphExec_t *exec_out)
+{
+    for (auto &c : g->graphs)
+        if (c.key == key) {
+            *exec_out = c.exec;
+            return PR_OK;
+        }
+    cudaGraph_t top = nullptr;
+    PR_CUDA(cudaGraphCreate(&top, 0));
+    auto fail = [&](cudaError_t e, const char *what) {
+        cudaGraphDestroy(top);
+        return cuda_status(e, what, __FILE__, __LINE__);
+    };
+    cudaGraphConditionalHandle h_outer, h_inner;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h_outer, top, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return fail(e, "outer handle");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h_outer;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t n_outer;
+    e = cudaGraphAddNode(&n_outer, top, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) return fail(e, "outer while");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaGraphConditionalHandleCreate(&h_inner, body, 0, 0);
+    if (e != cudaSuccess) return fail(e, "inner handle");
+    q.h_inner = h_inner;
+    q.h_outer = h_outer;
+    q.use_cond = 1;
+    inner.cond = h_inner;
+    inner.use_cond = 1;
+
+    cudaKernelNodeParams kp = {};
+    void *args_q[] = {&q};
+    kp.func = reinterpret_cast<void *>(&k_dc_resid<Te>);
+    kp.gridDim = dim3(grid_r);
+    kp.blockDim = dim3(SWEEP_BS);
+    kp.kernelParams = args_q;
+    cudaGraphNode_t n_r;
+    e = cudaGraphAddKernelNode(&n_r, body, nullptr, 0, &kp);
+    if (e != cudaSuccess) return fail(e, "residual node");
+
+    cudaGraphNodeParams ci = {};
+    ci.type = cudaGraphNodeTypeConditional;
+    ci.conditional.handle = h_inner;
+    ci.conditional.type = cudaGraphCondTypeWhile;
+    ci.conditional.size = 1;
+    cudaGraphNode_t n_inner;
+    e = cudaGraphAddNode(&n_inner, body, &n_r, nullptr, 1, &ci);
+    if (e != cudaSuccess) return fail(e, "inner while");
+    cudaGraph_t ibody = ci.conditional.phGraph_out[0];
+    void *args_s[] = {&inner};
+    kp.func = q.gs ? reinterpret_cast<void *>(&k_sweep<Te, float, true>)
+                   : reinterpret_cast<void *>(&k_sweep<Te, float, false>);
+    kp.gridDim = dim3(grid_s);
+    kp.kernelParams = args_s;
+    cudaGraphNode_t n_s;
+    e = cudaGraphAddKernelNode(&n_s, ibody, nullptr, 0, &kp);
+    if (e != cudaSuccess) return fail(e, "sweep node");
+
+    kp.func = reinterpret_cast<void *>(&k_dc_update<Te>);
+    kp.gridDim = dim3(grid_u);
+    kp.kernelParams = args_q;
+    cudaGraphNode_t n_u;
+    e = cudaGraphAddKernelNode(&n_u, body, &n_inner, 0, &kp);
+    if (e != cudaSuccess) return fail(e, "update node");
+
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, top, 0);
+    if (e != cudaSuccess) return fail(e, "instantiate");
+    pr_graph::Cached c;
+    c.key = key;
+    c.exec = exec;
+    c.graph = top;
+    g->graphs.push_back(c);
+    *exec_out = exec;
+    return PR_OK;
+}
+
+template <typename Te>
+static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, double *x_out,
+                        pr_result *res, cudaStream_t s)
+{
+    const int32_t n = g->n;
+    PR_TRY(buf_alloc(g, g->xbuf, sizeof(double) * (size_t)n, s));
+    PR_TRY(buf_alloc(g, g->rbuf, sizeof(float) * (size_t)n, s));
+    const bool gs = o->variant == PR_FUSED_GS;
+    const bool fp16 = o->precision == PR_FP16_DC;
+
+    SolveState *sx = g->state.as<SolveState>();
+    SolveState *se = sx + 1;
+    DCParams q;
+    memset(&q, 0, sizeof(q));
+    fill_params(g, q.p, true, s);
+    q.p.y0 = g->xbuf.p;
+    q.p.y1 = g->xbuf.p;
+    q.p.st = sx;
+    q.r32 = g->rbuf.as<float>();
+    SweepParams inner;
+    fill_params(g, inner, false, s);  // e buffers in ybuf, inv32
+    q.e0 = inner.y0;
+    q.e1 = inner.y1;
+    q.inv32 = g->inv32.as<float>();
+    q.inv64 = g->inv64.as<double>();
+    q.y64 = g->xbuf.as<double>();
+    q.sx = sx;
+    q.se = se;
+    q.gs = gs ? 1 : 0;
+    q.fp16 = fp16 ? 1 : 0;
+    inner.rhs = q.r32;
+    inner.st = se;
+    inner.st_outer = sx;
+    inner.dc = 1;
+    inner.renorm = 0;
+
+    SolveState *hs = g->host_state;
+    init_state(g, o, hs[0]);
+    hs[0].max_outer = o->max_outer > 0 ? o->max_outer : default_max_outer(o->precision);
+    hs[0].inner_rel = o->inner_rel > 0 ? o->inner_rel : default_eta(o->precision);
+    memset(&hs[1], 0, sizeof(SolveState));
+    hs[1].d = o->d;
+    hs[1].base = hs[0].base;
+    hs[1].inv_n = hs[0].inv_n;
+    hs[1].sigma = 1.0;
+    hs[1].max_iter = 256;  // per inner solve
+    hs[1].done = 1;
+    PR_CUDA(cudaMemcpyAsync(sx, hs, 2 * sizeof(SolveState), cudaMemcpyHostToDevice, s));
+    const int ib = std::max(1, std::min<int>((n + 255) / 256, g->num_sms * 8));
+    k_init<double, double><<<ib, 256, 0, s>>>(n, o->x0, q.p.outdeg, q.inv64, q.y64, sx, 1);
+    note_launch();
+    k_dc_first_scale<<<1, 1, 0, s>>>(sx, q.fp16, (double)n);
+    note_launch();
+    PR_LAUNCH_CHECK();
+
+    const void *f_r = reinterpret_cast<const void *>(&k_dc_resid<Te>);
+    const void *f_s = gs ? reinterpret_cast<const void *>(&k_sweep<Te, float, true>)
+                         : reinterpret_cast<const void *>(&k_sweep<Te, float, false>);
+    const unsigned grid_r = sweep_grid(g, q.p, f_r);
+    const unsigned grid_s = sweep_grid(g, inner, f_s);
+    const unsigned grid_u = (unsigned)ib;
+    bool graph_loop = false;
+    if (o->use_graph) {
+        const int key = 16 | (gs ? 2 : 0) | ((int)o->precision << 8);
+        cudaGraphExec_t exec;
+        PR_TRY(dc_graph<Te>(g, key, q, inner, grid_r, grid_s, grid_u, &exec));
+        PR_CUDA(cudaGraphLaunch(exec, s));
+        graph_loop = true;
+    } else {
+        q.use_cond = 0;
+        inner.use_cond = 0;
+        void *aq[] = {&q};
+        void *as[] = {&inner};
+        for (int outer = 0; outer < 1000; ++outer) {
+            PR_CUDA(cudaLaunchKernel(f_r, dim3(grid_r), dim3(SWEEP_BS), aq, 0, s));
+            note_launch();
+            PR_CUDA(cudaMemcpyAsync(hs, sx, 2 * sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+            PR_CUDA(cudaStreamSynchronize(s));
+            if (hs[0].done) break;
+            while (true) {
+                for (int k = 0; k < 8; ++k) {
+                    PR_CUDA(cudaLaunchKernel(f_s, dim3(grid_s), dim3(SWEEP_BS), as, 0, s));
+                    note_launch();
+                }
+                PR_CUDA(cudaMemcpyAsync(hs, sx, 2 * sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+                PR_CUDA(cudaStreamSynchronize(s));
+                if (hs[1].done) break;
+            }
+            PR_CUDA(cudaLaunchKernel(reinterpret_cast<const void *>(&k_dc_update<Te>),
+                                     dim3(grid_u), dim3(256), aq, 0, s));
+            note_launch();
+        }
+    }
+    k_output<double><<<ib, 256, 0, s>>>(n, q.p.outdeg, q.y64, q.y64, 0, sx, x_out);
+    note_launch();
+    PR_LAUNCH_CHECK();
+    PR_CUDA(cudaMemcpyAsync(hs, sx, 2 * sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    if (graph_loop) note_launch((uint64_t)hs[0].iter + hs[0].outer_iter);
+    pr_status st = (pr_status)hs[0].status;
+    if (res) {
+        res->outer_iters = hs[0].outer_iter;
+        res->iters = hs[0].iter - hs[0].outer_iter;
+        res->residual = hs[0].norm ? hs[0].resmax : hs[0].res;
+        res->sum_before_norm = hs[0].sigma * hs[0].sum;
+        res->status = st;
+    }
+    return st;
+}
+
+pr_status solve_dc(pr_graph *g, const pr_options *o, const pr_tune &tn, double *x_out,
+                   pr_result *res, cudaStream_t s)
+{
+    switch (o->precision) {
+    case PR_FP32_DC: return run_dc<float>(g, o, tn, x_out, res, s);
+    case PR_BF16_DC: return run_dc<__nv_bfloat16>(g, o, tn, x_out, res, s);
+    case PR_FP16_DC: return run_dc<__half>(g, o, tn, x_out, res, s);
+    default:
+        set_error("not a defect-correction precision");
+        return PR_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace fpr
