@@ -303,7 +303,15 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per sweep launch from an ncu capture (reported as is)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "sweeps"],
+                    help="sweeps: only build the workload graph and run --sweeps plain "
+                         "sweeps as separate launches (for profiler captures)")
+    ap.add_argument("--sweeps", type=int, default=4)
+    ap.add_argument("--variant", default="jacobi", choices=["jacobi", "gs"])
     args = ap.parse_args()
+    if args.mode == "sweeps":
+        run_sweeps(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -328,6 +336,24 @@ def main():
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
+
+
+def run_sweeps(args):
+    """Graph build plus a few sweeps launched one by one (no CUDA graph), so a
+    profiler sees each sweep kernel as its own launch."""
+    import torch
+
+    import paper_2203_09284_gb300 as fp
+    n, src_h, dst_h = workload(args.scale)
+    dev = torch.device("cuda", 0)
+    g = fp.Graph(n, torch.from_numpy(src_h).to(dev), torch.from_numpy(dst_h).to(dev))
+    x, r = g.solve(variant=args.variant, precision=args.precision, threshold=0.0,
+                   max_iter=args.sweeps, use_graph=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "sweeps", "n": n, "edges": len(src_h), "sweeps": r.iters,
+                      "outer": r.outer_iters, "precision": args.precision,
+                      "variant": args.variant}))
+    g.close()
 
 
 def reference_arm(args):
