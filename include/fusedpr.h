@@ -83,16 +83,19 @@ typedef struct {
 } pr_allocator;
 
 /* Launch parameters of the sweep (chosen by the autotuner; zero fields take
- * the library defaults). */
+ * the library defaults).  The sweep works in a degree-ordered numbering
+ * (in-degree descending), where the in-degree bins are contiguous. */
 typedef struct {
-    int32_t t_lo;      /* in-degree <= t_lo: thread per vertex (default 8) */
-    int32_t t_hub;     /* in-degree >  t_hub: block per vertex, split in
-                          segments of hub_seg edges (default 2048) */
-    int32_t hub_seg;   /* edges per hub segment (default 8192) */
-    int32_t low_rounds;/* vertices per thread in a low-degree chunk (default 4) */
-    int32_t mid_per_warp; /* mid vertices per warp in a mid chunk (default 4) */
-    int32_t deterministic_gs; /* 1: fused sweep in strict id order on one CTA
-                                 (reproduces Eq. 9 exactly; n <= 65536) */
+    int32_t t_lo;      /* in-degree <= t_lo: thread per vertex (default 16) */
+    int32_t t_hub;     /* in-degree >  t_hub: block per vertex, split into
+                          segments of hub_seg in-edges (default 1024,
+                          at most 4096) */
+    int32_t hub_seg;   /* in-edges per hub segment (default 4096) */
+    int32_t tile;      /* work units (in-edges + vertices) per tile of
+                          non-hub vertices, staged in shared memory
+                          (default 2048, 256 to 4096) */
+    int32_t deterministic_gs; /* 1: fused sweep in strict input id order on
+                                 one warp (reproduces Eq. 9; n <= 65536) */
 } pr_tune;
 
 typedef struct {
@@ -127,7 +130,11 @@ pr_status pr_options_default(pr_options *o);
  * Builds the graph on the device from an edge list (Sec. 3 storage):
  * out/in-degree histograms, the in-lists (CSC: column u = sources of u's
  * in-edges, ascending, ties by input position), inverse out-degrees
- * (IEEE 1.0/deg, 0 for dangling), in-degree bins and sweep work items.
+ * (IEEE 1.0/deg, 0 for dangling), and the sweep's working copy in a
+ * degree-ordered numbering: vertices sorted by in-degree, largest first (ties
+ * by id), in-lists re-sorted in the new ids.  That puts the in-degree bins in
+ * contiguous ranges and packs the most-gathered contributions together.
+ * Results of every solve are returned in the input ids.
  *   n       vertices, >= 1
  *   m       edges, 0 <= m < 2^31
  *   src,dst device int32 [m]; ids must lie in [0, n) (checked on the
@@ -149,7 +156,8 @@ pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_
 void pr_graph_destroy(pr_graph *g);
 
 /* Host outputs (each nullable): vertex and edge counts, dangling vertices,
- * and the sizes of the low/mid/hub in-degree bins. */
+ * and the sizes of the low/mid/hub in-degree bins under the graph's current
+ * thresholds (low: in-degree <= t_lo, hub: > t_hub). */
 pr_status pr_graph_info(const pr_graph *g, int32_t *n, int64_t *m, int32_t *n_dangling,
                         int32_t *bin_counts3);
 
@@ -157,13 +165,15 @@ pr_status pr_graph_info(const pr_graph *g, int32_t *n, int64_t *m, int32_t *n_da
  * Copies the build products to caller device buffers (each nullable), for
  * bit-exact checks: outdeg/indeg [n], col_ptr/row_ptr [n+1], row_idx/csc_eid
  * [m] (in-lists), col_idx/csr_eid [m] (out-lists, ordered by (dst, input
- * position); built on demand), inv_outdeg [n] (FP64), bins [n] (low, then
- * mid, then hub vertex ids, each ascending).
+ * position); built on demand), inv_outdeg [n] (FP64); the degree-ordered
+ * numbering: new_to_old [n], rcol_ptr [n+1], rrow_idx [m] (in-lists in the
+ * new ids, sources ascending, ties by input position).
  */
 pr_status pr_graph_export(pr_graph *g, int32_t *outdeg, int32_t *indeg, int32_t *col_ptr,
                           int32_t *row_idx, int32_t *csc_eid, int32_t *row_ptr,
                           int32_t *col_idx, int32_t *csr_eid, double *inv_outdeg,
-                          int32_t *bins, void *stream);
+                          int32_t *new_to_old, int32_t *rcol_ptr, int32_t *rrow_idx,
+                          void *stream);
 
 /*
  * Solves for the PageRank vector.

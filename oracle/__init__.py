@@ -57,6 +57,8 @@ def _load():
             lib = ctypes.CDLL(_SO)
             lib.orc_build.argtypes = [ctypes.c_int32, ctypes.c_int64, _I32, _I32, _I32, _I32,
                                       _I32, _I32, _I32, _I32, _I32, _I32, _F64]
+            lib.orc_relabel.argtypes = [ctypes.c_int32, ctypes.c_int64, _I32, _I32, _I32, _I32,
+                                        _I32, _I32, _I32]
             lib.orc_bins.argtypes = [ctypes.c_int32, _I32, ctypes.c_int32, ctypes.c_int32,
                                      _I32, _I32, _I32, _I32]
             lib.orc_bins.restype = None
@@ -143,6 +145,21 @@ def build_graph(n: int, src, dst) -> Graph:
         raise ValueError(f"orc_build failed ({rc})")
     return Graph(n, m, src, dst, outdeg, indeg, row_ptr, col_idx[:m], csr_eid[:m], col_ptr,
                  row_idx[:m], csc_eid[:m], inv)
+
+
+def relabel(g: Graph):
+    """Degree-ordered relabelling: new_to_old (in-degree descending, ties by
+    id) and the in-lists in the new ids (rcol_ptr, rrow_idx, rcsc_eid)."""
+    lib = _load()
+    n2o = np.empty(g.n, np.int32)
+    rcol = np.empty(g.n + 1, np.int32)
+    rrow = np.empty(max(g.m, 1), np.int32)
+    reid = np.empty(max(g.m, 1), np.int32)
+    rc = lib.orc_relabel(g.n, g.m, _p(g.src, _I32), _p(g.dst, _I32), _p(g.indeg, _I32),
+                         _p(n2o, _I32), _p(rcol, _I32), _p(rrow, _I32), _p(reid, _I32))
+    if rc != OK:
+        raise ValueError(f"orc_relabel failed ({rc})")
+    return n2o, rcol, rrow[:g.m], reid[:g.m]
 
 
 def bins(g: Graph, t_lo: int, t_hub: int):

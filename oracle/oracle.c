@@ -123,6 +123,52 @@ int orc_build(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
     return ORC_OK;
 }
 
+/*
+ * Degree-ordered relabelling used by the GPU sweep (an internal order; the
+ * results are returned in the original ids).  new_to_old lists the vertices
+ * by in-degree, largest first, ties in increasing id (a stable sort); the
+ * relabelled in-lists hold, for new column u' = old vertex new_to_old[u'],
+ * the new ids of its in-neighbours in ascending new id, ties by edge id.
+ * rcol_ptr has n+1 entries, rrow_idx and rcsc_eid m each.
+ */
+int orc_relabel(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                const int32_t *indeg, int32_t *new_to_old, int32_t *rcol_ptr,
+                int32_t *rrow_idx, int32_t *rcsc_eid)
+{
+    int32_t maxd = 0;
+    for (int32_t u = 0; u < n; ++u) if (indeg[u] > maxd) maxd = indeg[u];
+    /* counting sort of vertex ids by key maxd - indeg (stable) */
+    int32_t *key = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *o2n = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *nsrc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int32_t *ndst = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int32_t *eids = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int32_t *tmp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(m > 0 ? m : 1));
+    int rc = ORC_OK;
+    if (!key || !ids || !o2n || !nsrc || !ndst || !eids || !tmp) rc = ORC_ERR_OOM;
+    if (rc == ORC_OK) {
+        for (int32_t u = 0; u < n; ++u) { key[u] = maxd - indeg[u]; ids[u] = u; }
+        rc = counting_sort(n, maxd + 1, key, ids, new_to_old, NULL);
+    }
+    if (rc == ORC_OK) {
+        for (int32_t k = 0; k < n; ++k) o2n[new_to_old[k]] = k;
+        for (int64_t e = 0; e < m; ++e) {
+            nsrc[e] = o2n[src[e]];
+            ndst[e] = o2n[dst[e]];
+            eids[e] = (int32_t)e;
+        }
+        /* in-lists by (new dst, new src, edge id): sort by new src, then
+         * stably by new dst */
+        rc = counting_sort(m, n, nsrc, eids, tmp, NULL);
+    }
+    if (rc == ORC_OK) rc = counting_sort(m, n, ndst, tmp, rcsc_eid, rcol_ptr);
+    if (rc == ORC_OK)
+        for (int64_t q = 0; q < m; ++q) rrow_idx[q] = nsrc[rcsc_eid[q]];
+    free(key); free(ids); free(o2n); free(nsrc); free(ndst); free(eids); free(tmp);
+    return rc;
+}
+
 /* Stable partition of vertex ids by in-degree: low (<= t_lo), mid
  * (t_lo < deg <= t_hub) and hub (> t_hub), each list in ascending id order.
  * counts[0..2] receive the list lengths. */

@@ -42,8 +42,7 @@ NORMS = {"l1": PR_NORM_L1, "linf": PR_NORM_LINF}
 
 class PrTune(ctypes.Structure):
     _fields_ = [("t_lo", ctypes.c_int32), ("t_hub", ctypes.c_int32), ("hub_seg", ctypes.c_int32),
-                ("low_rounds", ctypes.c_int32), ("mid_per_warp", ctypes.c_int32),
-                ("deterministic_gs", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("deterministic_gs", ctypes.c_int32)]
 
 
 class PrOptions(ctypes.Structure):
@@ -109,7 +108,7 @@ def lib():
             L.pr_graph_destroy.restype = None
             L.pr_graph_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64),
                                         ctypes.POINTER(i32), ctypes.POINTER(i32)]
-            L.pr_graph_export.argtypes = [vp] + [vp] * 10 + [vp]
+            L.pr_graph_export.argtypes = [vp] + [vp] * 12 + [vp]
             L.pr_solve.argtypes = [vp, ctypes.POINTER(PrOptions), vp, ctypes.POINTER(PrResult), vp]
             L.pr_solve_batched.argtypes = [vp, ctypes.POINTER(PrOptions), i32, vp, vp,
                                            ctypes.POINTER(PrResult), vp]
@@ -235,7 +234,8 @@ def pr_graph_export(handle, stream=None, csr=False):
         "col_ptr": torch.empty(n + 1, **i32), "row_idx": torch.empty(m, **i32),
         "csc_eid": torch.empty(m, **i32), "inv_outdeg": torch.empty(n, dtype=torch.float64,
                                                                     device=dev),
-        "bins": torch.empty(n, **i32),
+        "new_to_old": torch.empty(n, **i32), "rcol_ptr": torch.empty(n + 1, **i32),
+        "rrow_idx": torch.empty(m, **i32),
     }
     if csr:
         out.update(row_ptr=torch.empty(n + 1, **i32), col_idx=torch.empty(m, **i32),
@@ -244,13 +244,14 @@ def pr_graph_export(handle, stream=None, csr=False):
     st = lib().pr_graph_export(ctypes.c_void_p(handle), _ptr(g("outdeg")), _ptr(g("indeg")),
                                _ptr(g("col_ptr")), _ptr(g("row_idx")), _ptr(g("csc_eid")),
                                _ptr(g("row_ptr")), _ptr(g("col_idx")), _ptr(g("csr_eid")),
-                               _ptr(g("inv_outdeg")), _ptr(g("bins")), _stream(stream))
+                               _ptr(g("inv_outdeg")), _ptr(g("new_to_old")),
+                               _ptr(g("rcol_ptr")), _ptr(g("rrow_idx")), _stream(stream))
     _check(st, "pr_graph_export")
     return out
 
 
 def make_options(d=0.85, threshold=1e-10, max_iter=1000, variant="jacobi", precision="fp64",
-                 norm="l1", x0=None, history=None, use_graph=True, max_outer=8, inner_rel=0.0,
+                 norm="l1", x0=None, history=None, use_graph=True, max_outer=0, inner_rel=0.0,
                  tune=None):
     o = pr_options_default()
     o.d, o.threshold, o.max_iter = float(d), float(threshold), int(max_iter)

@@ -98,26 +98,25 @@ struct SolveState {
     double *history;
 };
 
-// Work decomposition of a sweep over the in-degree bins: a run of blocks per
-// bin role, in the order hub segments, mid chunks, low chunks.
+// Work decomposition of a sweep in the degree-ordered ids (in-degree
+// descending, so the in-degree bins are contiguous ranges):
+//   hubs  [0, nhub)        in-degree > t_hub: segments of hub_seg in-edges,
+//                          one block each
+//   tiles [nhub, n)        consecutive vertices with at most tile_c units of
+//                          work (in-edges + vertices); in a tile, in-degree
+//                          > t_lo (mid) is reduced by a warp per vertex,
+//                          the rest by a thread per vertex
 struct Items {
-    int32_t t_lo = -1, t_hub = -1, hub_seg = 0;
-    int32_t nlow = 0, nmid = 0, nhub = 0;
-    int32_t nhubseg = 0;          // blocks of the hub role
-    int32_t low_rounds = 4;       // vertices per thread in a low chunk
-    int32_t mid_per_warp = 4;     // vertices per warp in a mid chunk
-    Buf bins;                     // [n] low | mid | hub vertex ids
+    int32_t t_lo = -1, t_hub = -1, hub_seg = 0, tile_c = 0;
+    int32_t nhub = 0, nmid = 0, nlow = 0;
+    int32_t nhubseg = 0;          // items of the hub role
+    int32_t ntiles = 0;           // items of the tile role
+    int32_t maxe = 0;             // largest in-edge count of a tile
     Buf hubseg_start;             // [nhub + 1] first segment of each hub
     Buf seg_acc;                  // [nhubseg] double partial sums
     Buf hub_cnt;                  // [nhub] segments finished this sweep
-    int32_t low_blocks(int bs) const {
-        int per = bs * low_rounds;
-        return (nlow + per - 1) / per;
-    }
-    int32_t mid_blocks(int bs) const {
-        int per = (bs / 32) * mid_per_warp;
-        return (nmid + per - 1) / per;
-    }
+    Buf tile_start;               // [ntiles + 1] first vertex of each tile
+    Buf tile_mid;                 // [ntiles] first thread-per-vertex vertex
 };
 
 }  // namespace fpr
@@ -132,14 +131,18 @@ struct pr_graph {
     fpr::Mem mem;
     std::vector<fpr::Buf *> owned;
 
-    // build products
+    // build products in the input ids
     fpr::Buf outdeg, indeg, col_ptr, row_idx, csc_eid;
     fpr::Buf row_ptr, col_idx, csr_eid;  // out-lists (lazy)
-    fpr::Buf inv64, inv32;               // 1/outdeg (0 for dangling)
+    fpr::Buf inv64;                      // 1/outdeg (0 for dangling)
+    // degree-ordered ids used by the sweeps (r_ = relabelled)
+    fpr::Buf n2o, o2n;                   // new -> old, old -> new
+    fpr::Buf r_outdeg, r_col_ptr, r_row_idx, r_csc_eid, r_inv64, r_inv32;
     fpr::Items items;
     pr_tune tune{};
 
-    // weighted graphs: raw weights and row-normalised P per in-list slot
+    // weighted graphs: raw weights, row sums (input ids) and P per
+    // relabelled in-list slot
     bool weighted = false;
     fpr::Buf w, rowsum, p64_csc, p32_csc;
 
@@ -172,6 +175,25 @@ void release_graphs(pr_graph *g);
 // exclusive scan of `count` int32 values; out[count] receives the total.
 pr_status scan_exclusive(pr_graph *g, const int32_t *in, int32_t *out, int64_t count,
                          cudaStream_t s);
+// stable LSD radix sort of (key, value) pairs by the 8-bit digits at `shifts`
+// (alt_k/alt_v: same-size scratch; the result ends in keys/vals)
+pr_status radix_sort(pr_graph *g, uint64_t *keys, int32_t *vals, uint64_t *alt_k, int32_t *alt_v,
+                     int64_t m, const std::vector<int> &shifts, cudaStream_t s);
+// digit shifts covering ids < n, starting at bit `offset`
+std::vector<int> digit_shifts(int32_t n, int offset);
+
+// primitives.cu kernels launched by the graph assembly
+__global__ void k_degrees(int64_t m, const int32_t *__restrict__ src,
+                          const int32_t *__restrict__ dst, int32_t n, int32_t *outdeg,
+                          int32_t *indeg, int32_t *err);
+__global__ void k_make_csc_keys(int64_t m, const int32_t *__restrict__ src,
+                                const int32_t *__restrict__ dst, uint64_t *keys, int32_t *vals);
+__global__ void k_split_keys(int64_t m, const uint64_t *__restrict__ keys, int32_t *low32);
+__global__ void k_make_csr_keys(int32_t n, const int32_t *__restrict__ col_ptr,
+                                const int32_t *__restrict__ row_idx,
+                                const int32_t *__restrict__ csc_eid, uint64_t *keys, int32_t *vals);
+__global__ void k_split_csr(int64_t m, const uint64_t *__restrict__ keys, int32_t *col_idx);
+const char *last_error();
 
 // ------------------------------------------------------------ device side --
 __device__ __forceinline__ double warp_sum(double v)

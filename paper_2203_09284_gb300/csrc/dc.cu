@@ -27,7 +27,7 @@ struct DCParams {
     SweepParams p;           // traversal of the FP64 residual sweep (y0 = Y64)
     float *r32;              // right-hand side of the correction solve
     void *e0, *e1;           // correction buffers (stored form)
-    const float *inv32;
+    const float *inv32;      // degree-ordered 1/outdeg
     const double *inv64;
     double *y64;
     SolveState *sx, *se;     // outer and inner states
@@ -35,6 +35,7 @@ struct DCParams {
     int use_cond;
     int gs;                  // inner sweeps are fused (in place)
     int fp16;                // scale the correction into the FP16 range
+    int weighted;
 };
 
 // Epilogue of the residual sweep: r_u in FP64, stored as FP32, and the first
@@ -50,14 +51,15 @@ struct ResidFin {
     __device__ __forceinline__ double operator()(int u, double acc)
     {
         const int od = q.p.outdeg[u];
+        const bool plain = q.weighted || od == 0;  // stored value is x itself
         const double yo = __ldg(q.y64 + u);
-        const double xold = od > 0 ? yo * static_cast<double>(od) : yo;
+        const double xold = plain ? yo : yo * static_cast<double>(od);
         const double xnew = c.base + c.d * (c.sig * (acc + c.dt));
         const double r = xnew - c.sig * xold;
         const float rf = static_cast<float>(r);
         q.r32[u] = rf;
         const float es = rf * rscale;
-        static_cast<Te *>(q.e0)[u] = from_a<Te>(od > 0 ? es * q.inv32[u] : es);
+        static_cast<Te *>(q.e0)[u] = from_a<Te>(plain ? es : es * q.inv32[u]);
         const double ar = fabs(r);
         pt.l1 += ar;
         pt.lmax = ar > pt.lmax ? ar : pt.lmax;
@@ -78,7 +80,7 @@ __device__ __forceinline__ double next_scale(const SolveState *sx, int fp16, dou
     return ldexp(1.0, -k);
 }
 
-template <typename Te>
+template <typename Te, bool W>
 __global__ void __launch_bounds__(SWEEP_BS, 4) k_dc_resid(DCParams q)
 {
     SolveState *sx = q.sx, *se = q.se;
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(SWEEP_BS, 4) k_dc_resid(DCParams q)
         return;
     }
     ResidFin<Te> fin(q, load_ctx<double>(sx), static_cast<float>(1.0 / sx->scale));
-    run_items<double, double, false>(q.p, q.y64, fin);
+    run_items<double, double, false, W>(q.p, q.y64, fin);
     block_partials<double>(sx, fin.pt);
     if (!(last_block(sx) && threadIdx.x == 0)) return;
     double res, resmax, dang_e, sum_e;
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(SWEEP_BS, 4) k_dc_resid(DCParams q)
     const double err = sx->norm ? resmax : res;
     if (sx->history) sx->history[total - 1] = err;
     const bool conv = err <= sx->tau;
-    bool go_on = !(conv || sx->outer_iter >= sx->max_outer || total >= sx->max_iter);
+    const bool go_on = !(conv || sx->outer_iter >= sx->max_outer || total >= sx->max_iter);
     if (!go_on) {
         sx->done = 1;
         sx->status = conv ? PR_OK : PR_NOT_CONVERGED;
@@ -136,12 +138,13 @@ __global__ void k_dc_update(DCParams q)
     const int n = q.p.n;
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
         const int od = q.p.outdeg[u];
+        const bool plain = q.weighted || od == 0;
         const double yx = q.y64[u];
-        const double xs = od > 0 ? yx * static_cast<double>(od) : yx;
+        const double xs = plain ? yx : yx * static_cast<double>(od);
         const float ev = to_a<float>(eb[u]);
-        const float es = od > 0 ? ev * static_cast<float>(od) : ev;
+        const float es = plain ? ev : ev * static_cast<float>(od);
         const double xn = sgx * xs + sge * static_cast<double>(es);
-        q.y64[u] = od > 0 ? xn * q.inv64[u] : xn;
+        q.y64[u] = plain ? xn : xn * q.inv64[u];
         pt.sm += xn;
         if (od == 0) pt.dm += xn;
     }
@@ -183,10 +186,14 @@ static int default_max_outer(pr_precision pr)
     }
 }
 
-template <typename Te>
+struct DCLaunch {
+    const void *f_r, *f_s, *f_u;
+    unsigned grid_r, grid_s, grid_u;
+    size_t smem_r, smem_s;
+};
+
 static pr_status dc_graph(pr_graph *g, int key, DCParams &q, SweepParams &inner,
-                          unsigned grid_r, unsigned grid_s, unsigned grid_u,
-                          cudaGraphExec_t *exec_out)
+                          const DCLaunch &L, cudaGraphExec_t *exec_out)
 {
     for (auto &c : g->graphs)
         if (c.key == key) {
@@ -219,11 +226,13 @@ static pr_status dc_graph(pr_graph *g, int key, DCParams &q, SweepParams &inner,
     inner.cond = h_inner;
     inner.use_cond = 1;
 
+    // body: residual -> WHILE(inner) { correction sweep } -> update
     cudaKernelNodeParams kp = {};
     void *args_q[] = {&q};
-    kp.func = reinterpret_cast<void *>(&k_dc_resid<Te>);
-    kp.gridDim = dim3(grid_r);
+    kp.func = const_cast<void *>(L.f_r);
+    kp.gridDim = dim3(L.grid_r);
     kp.blockDim = dim3(SWEEP_BS);
+    kp.sharedMemBytes = (unsigned)L.smem_r;
     kp.kernelParams = args_q;
     cudaGraphNode_t n_r;
     e = cudaGraphAddKernelNode(&n_r, body, nullptr, 0, &kp);
@@ -239,19 +248,20 @@ static pr_status dc_graph(pr_graph *g, int key, DCParams &q, SweepParams &inner,
     if (e != cudaSuccess) return fail(e, "inner while");
     cudaGraph_t ibody = ci.conditional.phGraph_out[0];
     void *args_s[] = {&inner};
-    kp.func = q.gs ? reinterpret_cast<void *>(&k_sweep<Te, float, true>)
-                   : reinterpret_cast<void *>(&k_sweep<Te, float, false>);
-    kp.gridDim = dim3(grid_s);
+    kp.func = const_cast<void *>(L.f_s);
+    kp.gridDim = dim3(L.grid_s);
+    kp.sharedMemBytes = (unsigned)L.smem_s;
     kp.kernelParams = args_s;
     cudaGraphNode_t n_s;
     e = cudaGraphAddKernelNode(&n_s, ibody, nullptr, 0, &kp);
     if (e != cudaSuccess) return fail(e, "sweep node");
 
-    kp.func = reinterpret_cast<void *>(&k_dc_update<Te>);
-    kp.gridDim = dim3(grid_u);
+    kp.func = const_cast<void *>(L.f_u);
+    kp.gridDim = dim3(L.grid_u);
+    kp.sharedMemBytes = 0;
     kp.kernelParams = args_q;
     cudaGraphNode_t n_u;
-    e = cudaGraphAddKernelNode(&n_u, body, &n_inner, 0, &kp);
+    e = cudaGraphAddKernelNode(&n_u, body, &n_inner, 1, &kp);  // after the inner loop
     if (e != cudaSuccess) return fail(e, "update node");
 
     cudaGraphExec_t exec = nullptr;
@@ -275,27 +285,29 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     PR_TRY(buf_alloc(g, g->rbuf, sizeof(float) * (size_t)n, s));
     const bool gs = o->variant == PR_FUSED_GS;
     const bool fp16 = o->precision == PR_FP16_DC;
+    const bool weighted = g->weighted;
 
     SolveState *sx = g->state.as<SolveState>();
     SolveState *se = sx + 1;
     DCParams q;
     memset(&q, 0, sizeof(q));
-    fill_params(g, q.p, true, s);
+    fill_params(g, q.p, true, sizeof(double));
     q.p.y0 = g->xbuf.p;
     q.p.y1 = g->xbuf.p;
     q.p.st = sx;
     q.r32 = g->rbuf.as<float>();
     SweepParams inner;
-    fill_params(g, inner, false, s);  // e buffers in ybuf, inv32
+    fill_params(g, inner, false, sizeof(Te));  // correction buffers in ybuf, FP32 1/outdeg
     q.e0 = inner.y0;
     q.e1 = inner.y1;
-    q.inv32 = g->inv32.as<float>();
-    q.inv64 = g->inv64.as<double>();
+    q.inv32 = g->r_inv32.as<float>();
+    q.inv64 = g->r_inv64.as<double>();
     q.y64 = g->xbuf.as<double>();
     q.sx = sx;
     q.se = se;
     q.gs = gs ? 1 : 0;
     q.fp16 = fp16 ? 1 : 0;
+    q.weighted = weighted ? 1 : 0;
     inner.rhs = q.r32;
     inner.st = se;
     inner.st_outer = sx;
@@ -315,23 +327,28 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     hs[1].done = 1;
     PR_CUDA(cudaMemcpyAsync(sx, hs, 2 * sizeof(SolveState), cudaMemcpyHostToDevice, s));
     const int ib = std::max(1, std::min<int>((n + 255) / 256, g->num_sms * 8));
-    k_init<double, double><<<ib, 256, 0, s>>>(n, o->x0, q.p.outdeg, q.inv64, q.y64, sx, 1);
+    k_init<double, double><<<ib, 256, 0, s>>>(n, o->x0, g->n2o.as<int32_t>(), q.p.outdeg, q.inv64,
+                                             q.y64, sx, 1, weighted ? 1 : 0);
     note_launch();
     k_dc_first_scale<<<1, 1, 0, s>>>(sx, q.fp16, (double)n);
     note_launch();
     PR_LAUNCH_CHECK();
 
-    const void *f_r = reinterpret_cast<const void *>(&k_dc_resid<Te>);
-    const void *f_s = gs ? reinterpret_cast<const void *>(&k_sweep<Te, float, true>)
-                         : reinterpret_cast<const void *>(&k_sweep<Te, float, false>);
-    const unsigned grid_r = sweep_grid(g, q.p, f_r);
-    const unsigned grid_s = sweep_grid(g, inner, f_s);
-    const unsigned grid_u = (unsigned)ib;
+    DCLaunch L;
+    L.f_r = weighted ? reinterpret_cast<const void *>(&k_dc_resid<Te, true>)
+                     : reinterpret_cast<const void *>(&k_dc_resid<Te, false>);
+    L.f_s = pick_sweep<Te, float>(gs, weighted);
+    L.f_u = reinterpret_cast<const void *>(&k_dc_update<Te>);
+    L.smem_r = sweep_smem<double, double>(g, false);
+    L.smem_s = sweep_smem<Te, float>(g, gs);
+    L.grid_r = sweep_grid(g, q.p, L.f_r, L.smem_r);
+    L.grid_s = sweep_grid(g, inner, L.f_s, L.smem_s);
+    L.grid_u = (unsigned)ib;
     bool graph_loop = false;
     if (o->use_graph) {
-        const int key = 16 | (gs ? 2 : 0) | ((int)o->precision << 8);
+        const int key = 16 | (gs ? 2 : 0) | (weighted ? 8 : 0) | ((int)o->precision << 8);
         cudaGraphExec_t exec;
-        PR_TRY(dc_graph<Te>(g, key, q, inner, grid_r, grid_s, grid_u, &exec));
+        PR_TRY(dc_graph(g, key, q, inner, L, &exec));
         PR_CUDA(cudaGraphLaunch(exec, s));
         graph_loop = true;
     } else {
@@ -340,26 +357,26 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
         void *aq[] = {&q};
         void *as[] = {&inner};
         for (int outer = 0; outer < 1000; ++outer) {
-            PR_CUDA(cudaLaunchKernel(f_r, dim3(grid_r), dim3(SWEEP_BS), aq, 0, s));
+            PR_CUDA(cudaLaunchKernel(L.f_r, dim3(L.grid_r), dim3(SWEEP_BS), aq, L.smem_r, s));
             note_launch();
             PR_CUDA(cudaMemcpyAsync(hs, sx, 2 * sizeof(SolveState), cudaMemcpyDeviceToHost, s));
             PR_CUDA(cudaStreamSynchronize(s));
             if (hs[0].done) break;
             while (true) {
                 for (int k = 0; k < 8; ++k) {
-                    PR_CUDA(cudaLaunchKernel(f_s, dim3(grid_s), dim3(SWEEP_BS), as, 0, s));
+                    PR_CUDA(cudaLaunchKernel(L.f_s, dim3(L.grid_s), dim3(SWEEP_BS), as, L.smem_s, s));
                     note_launch();
                 }
                 PR_CUDA(cudaMemcpyAsync(hs, sx, 2 * sizeof(SolveState), cudaMemcpyDeviceToHost, s));
                 PR_CUDA(cudaStreamSynchronize(s));
                 if (hs[1].done) break;
             }
-            PR_CUDA(cudaLaunchKernel(reinterpret_cast<const void *>(&k_dc_update<Te>),
-                                     dim3(grid_u), dim3(256), aq, 0, s));
+            PR_CUDA(cudaLaunchKernel(L.f_u, dim3(L.grid_u), dim3(256), aq, 0, s));
             note_launch();
         }
     }
-    k_output<double><<<ib, 256, 0, s>>>(n, q.p.outdeg, q.y64, q.y64, 0, sx, x_out);
+    k_output<double><<<ib, 256, 0, s>>>(n, g->o2n.as<int32_t>(), q.p.outdeg, q.y64, q.y64, 0, sx,
+                                       x_out, weighted ? 1 : 0);
     note_launch();
     PR_LAUNCH_CHECK();
     PR_CUDA(cudaMemcpyAsync(hs, sx, 2 * sizeof(SolveState), cudaMemcpyDeviceToHost, s));

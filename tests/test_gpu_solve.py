@@ -146,10 +146,10 @@ def test_closed_forms_on_gpu(gs):
     g.close()
 
 
-@pytest.mark.parametrize("tune", [{"t_lo": 2, "t_hub": 16, "hub_seg": 256},
-                                  {"t_lo": 32, "t_hub": 100000},
-                                  {"t_lo": 0, "t_hub": 0, "hub_seg": 512, "low_rounds": 1,
-                                   "mid_per_warp": 1}])
+@pytest.mark.parametrize("tune", [{"t_lo": 2, "t_hub": 16, "hub_seg": 256, "tile": 256},
+                                  {"t_lo": 32, "t_hub": 100000, "tile": 8192},
+                                  {"t_lo": 1, "t_hub": 1, "hub_seg": 512, "tile": 300},
+                                  {"t_lo": 64, "t_hub": 4096, "hub_seg": 1024, "tile": 1024}])
 def test_bin_thresholds_do_not_change_the_result(s16, tune):
     n, src, dst, og, g, star = s16
     x, r = g.solve(threshold=0.0, max_iter=6, tune=tune)

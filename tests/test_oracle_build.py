@@ -92,6 +92,33 @@ def test_storage_example_of_section_3():
         assert offs[int(slot)] == int(val)
 
 
+@pytest.mark.parametrize("case", ["rmat", "dups", "empty", "hub"])
+def test_relabel_matches_numpy(case):
+    if case == "rmat":
+        n, src, dst = gen.rmat(12, 16, seed=2)
+    elif case == "dups":
+        n, src, dst = gen.rmat(9, 8, seed=3, dedup=False)
+    elif case == "empty":
+        n, src, dst = 6, np.zeros(0, np.int32), np.zeros(0, np.int32)
+    else:
+        n = 300
+        src = np.arange(n - 1, 0, -1).astype(np.int32)
+        dst = np.zeros(n - 1, np.int32)
+    g = oracle.build_graph(n, src, dst)
+    n2o, rcol, rrow, reid = oracle.relabel(g)
+    want = np.argsort(-g.indeg.astype(np.int64), kind="stable")
+    assert np.array_equal(n2o, want)
+    o2n = np.empty(n, np.int64)
+    o2n[want] = np.arange(n)
+    ns, nd = o2n[src], o2n[dst]
+    order = np.lexsort((np.arange(len(src)), ns, nd))
+    assert np.array_equal(reid, order)
+    assert np.array_equal(rrow, ns[order])
+    assert np.array_equal(rcol, np.concatenate([[0], np.cumsum(np.bincount(nd, minlength=n))]))
+    # in-degrees in the new order are non-increasing
+    assert (np.diff(np.diff(rcol)) <= 0).all()
+
+
 def test_bins_are_stable_partition():
     n, src, dst = gen.rmat(12, 16, seed=4)
     g = oracle.build_graph(n, src, dst)
