@@ -96,6 +96,10 @@ typedef struct {
                           (default 2048, 256 to 4096) */
     int32_t deterministic_gs; /* 1: fused sweep in strict input id order on
                                  one warp (reproduces Eq. 9; n <= 65536) */
+    int32_t stage_kb;  /* shared memory (KB) per block for a copy of the
+                          stored vector's first entries, the most-gathered
+                          contributions in the degree-ordered ids (default
+                          64; -1 disables; at most 160) */
 } pr_tune;
 
 typedef struct {

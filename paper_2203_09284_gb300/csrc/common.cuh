@@ -112,6 +112,7 @@ struct Items {
     int32_t nhubseg = 0;          // items of the hub role
     int32_t ntiles = 0;           // items of the tile role
     int32_t maxe = 0;             // largest in-edge count of a tile
+    int32_t stage_kb = 64;        // shared-memory copy of the hottest sources
     Buf hubseg_start;             // [nhub + 1] first segment of each hub
     Buf seg_acc;                  // [nhubseg] double partial sums
     Buf hub_cnt;                  // [nhub] segments finished this sweep

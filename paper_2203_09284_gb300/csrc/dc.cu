@@ -281,7 +281,7 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
                         pr_result *res, cudaStream_t s)
 {
     const int32_t n = g->n;
-    PR_TRY(buf_alloc(g, g->xbuf, sizeof(double) * (size_t)n, s));
+    PR_TRY(buf_alloc(g, g->xbuf, sizeof(double) * (size_t)n + 64, s));  // 16-byte staged reads
     PR_TRY(buf_alloc(g, g->rbuf, sizeof(float) * (size_t)n, s));
     const bool gs = o->variant == PR_FUSED_GS;
     const bool fp16 = o->precision == PR_FP16_DC;
@@ -346,7 +346,8 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     L.grid_u = (unsigned)ib;
     bool graph_loop = false;
     if (o->use_graph) {
-        const int key = 16 | (gs ? 2 : 0) | (weighted ? 8 : 0) | ((int)o->precision << 8);
+        const int key = 16 | (gs ? 2 : 0) | (weighted ? 8 : 0) | ((int)o->precision << 8) |
+                        (g->items.stage_kb << 16);
         cudaGraphExec_t exec;
         PR_TRY(dc_graph(g, key, q, inner, L, &exec));
         PR_CUDA(cudaGraphLaunch(exec, s));

@@ -151,8 +151,10 @@ pr_tune effective_tune(const pr_graph *g, const pr_tune *t)
         if (t->t_hub > 0) r.t_hub = t->t_hub;
         if (t->hub_seg > 0) r.hub_seg = t->hub_seg;
         if (t->tile > 0) r.tile = t->tile;
+        if (t->stage_kb != 0) r.stage_kb = t->stage_kb;
         r.deterministic_gs = t->deterministic_gs;
     }
+    r.stage_kb = r.stage_kb < 0 ? 0 : std::min(r.stage_kb, 160);
     // a tile stages up to tile + t_hub in-edges in shared memory: both are
     // capped at 4096 (at most 128 KB per block for the FP64 fused sweep)
     r.t_hub = std::max(1, std::min(r.t_hub, 4096));
@@ -172,6 +174,7 @@ static void drop_temp(pr_graph *g, Buf &b, cudaStream_t s)
 pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
 {
     Items &it = g->items;
+    it.stage_kb = t.stage_kb;
     if (it.t_lo == t.t_lo && it.t_hub == t.t_hub && it.hub_seg == t.hub_seg &&
         it.tile_c == t.tile)
         return PR_OK;
@@ -527,6 +530,7 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
     g->tune.hub_seg = 4096;
     g->tune.tile = 2048;
     g->tune.deterministic_gs = 0;
+    g->tune.stage_kb = 64;
     pr_status st = PR_OK;
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess)

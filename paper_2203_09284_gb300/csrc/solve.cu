@@ -86,6 +86,7 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem)
     p.maxe = it.maxe;
     p.tile_start = it.tile_start.as<int32_t>();
     p.tile_mid = it.tile_mid.as<int32_t>();
+    p.stage = (int32_t)std::min<int64_t>(g->n, (int64_t)it.stage_kb * 1024 / (int64_t)elem);
     p.y0 = g->ybuf.p;
     p.y1 = static_cast<char *>(g->ybuf.p) + ((g->n * elem + 255) & ~(size_t)255);
     p.st = g->state.as<SolveState>();
@@ -221,8 +222,10 @@ template const void *pick_sweep<__half, float>(bool, bool);
 template <typename T, typename A>
 size_t sweep_smem(const pr_graph *g, bool gs)
 {
-    return gs ? tile_smem_bytes<T, A, true>(g->items.maxe, g->items.tile_c)
-              : tile_smem_bytes<T, A, false>(g->items.maxe, g->items.tile_c);
+    const int stage = (int)std::min<int64_t>(g->n, (int64_t)g->items.stage_kb * 1024 / sizeof(T));
+    return stage_bytes<T>(stage) +
+           (gs ? tile_smem_bytes<T, A, true>(g->items.maxe, g->items.tile_c)
+               : tile_smem_bytes<T, A, false>(g->items.maxe, g->items.tile_c));
 }
 template size_t sweep_smem<double, double>(const pr_graph *, bool);
 template size_t sweep_smem<float, float>(const pr_graph *, bool);
@@ -278,7 +281,8 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
     }
     bool graph_loop = false;
     if (o->use_graph) {
-        const int key = (fp64 ? 1 : 0) | (gs ? 2 : 0) | (serial ? 4 : 0) | (weighted ? 8 : 0);
+        const int key = (fp64 ? 1 : 0) | (gs ? 2 : 0) | (serial ? 4 : 0) | (weighted ? 8 : 0) |
+                        (g->items.stage_kb << 16);
         cudaGraphExec_t exec;
         PR_TRY(loop_graph(g, key, func, grid, block, smem, p, &exec));
         PR_CUDA(cudaGraphLaunch(exec, s));

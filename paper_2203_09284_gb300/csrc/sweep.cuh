@@ -61,6 +61,8 @@ struct SweepParams {
     int32_t ntiles, tile_c, maxe;
     const int32_t *tile_start;    // [ntiles + 1]
     const int32_t *tile_mid;      // [ntiles]
+    int32_t stage;                // y[0, stage) is copied to shared memory at
+                                  // the start of the sweep (hottest sources)
     void *y0, *y1;                // stored vectors
     const void *rhs;              // A[n] right-hand side, or null: (1-d)/n
     SolveState *st;
@@ -194,29 +196,43 @@ struct SweepFin {
     }
 };
 
+// Where a gathered contribution comes from: the copy of y[0, nstaged) in
+// shared memory (the hottest sources in the degree-ordered ids), else y.
+template <typename T, bool GS>
+struct Src {
+    const T *y;
+    const T *staged;
+    int nstaged;
+    __device__ __forceinline__ T operator()(int v) const
+    {
+        return v < nstaged ? staged[v] : ld_y<T, GS>(y, v);
+    }
+};
+
 // Sum over in-list slots [a, b) by one warp, 16-byte index loads in the body.
 template <typename T, typename A, bool GS, bool W>
-__device__ __forceinline__ A warp_gather(const SweepParams &p, const T *y, int a, int b, int lane)
+__device__ __forceinline__ A warp_gather(const SweepParams &p, const Src<T, GS> &y, int a, int b,
+                                         int lane)
 {
     const int32_t *__restrict__ row_idx = p.row_idx;
     A acc = 0;
     if (b - a < 64) {
         for (int i = a + lane; i < b; i += 32)
-            acc += edge_term<A, W>(p, i, to_a<A>(ld_y<T, GS>(y, row_idx[i])));
+            acc += edge_term<A, W>(p, i, to_a<A>(y(row_idx[i])));
         return acc;
     }
     const int a4 = (a + 3) & ~3;
     const int b4 = b & ~3;
-    if (lane < a4 - a) acc += edge_term<A, W>(p, a + lane, to_a<A>(ld_y<T, GS>(y, row_idx[a + lane])));
+    if (lane < a4 - a) acc += edge_term<A, W>(p, a + lane, to_a<A>(y(row_idx[a + lane])));
     for (int i = a4 + 4 * lane; i < b4; i += 128) {
         const int4 q = __ldg(reinterpret_cast<const int4 *>(row_idx + i));
-        const A s0 = edge_term<A, W>(p, i, to_a<A>(ld_y<T, GS>(y, q.x)));
-        const A s1 = edge_term<A, W>(p, i + 1, to_a<A>(ld_y<T, GS>(y, q.y)));
-        const A s2 = edge_term<A, W>(p, i + 2, to_a<A>(ld_y<T, GS>(y, q.z)));
-        const A s3 = edge_term<A, W>(p, i + 3, to_a<A>(ld_y<T, GS>(y, q.w)));
+        const A s0 = edge_term<A, W>(p, i, to_a<A>(y(q.x)));
+        const A s1 = edge_term<A, W>(p, i + 1, to_a<A>(y(q.y)));
+        const A s2 = edge_term<A, W>(p, i + 2, to_a<A>(y(q.z)));
+        const A s3 = edge_term<A, W>(p, i + 3, to_a<A>(y(q.w)));
         acc += (s0 + s1) + (s2 + s3);
     }
-    if (lane < b - b4) acc += edge_term<A, W>(p, b4 + lane, to_a<A>(ld_y<T, GS>(y, row_idx[b4 + lane])));
+    if (lane < b - b4) acc += edge_term<A, W>(p, b4 + lane, to_a<A>(y(row_idx[b4 + lane])));
     return acc;
 }
 
@@ -329,7 +345,8 @@ __device__ __forceinline__ void close_sweep(const SweepParams &p)
 // completes the hub's last segment adds the segment sums in order and calls
 // the epilogue (thread 0).
 template <typename T, typename A, bool GS, bool W, typename Fin>
-__device__ __forceinline__ void hub_segment(const SweepParams &p, int b, const T *yin, Fin &fin)
+__device__ __forceinline__ void hub_segment(const SweepParams &p, int b, const Src<T, GS> &yin,
+                                            Fin &fin)
 {
     __shared__ double red[SWEEP_BS / 32];
     __shared__ int sh_h;
@@ -385,8 +402,8 @@ __host__ __device__ constexpr size_t tile_smem_bytes(int maxe, int tile_c)
 }
 
 template <typename T, typename A, bool GS, bool W, typename Fin>
-__device__ __forceinline__ void tile_item(const SweepParams &p, int k, const T *yin, Fin &fin,
-                                          unsigned char *smem)
+__device__ __forceinline__ void tile_item(const SweepParams &p, int k, const Src<T, GS> &yin,
+                                          Fin &fin, unsigned char *smem)
 {
     const int v0 = p.tile_start[k], v1 = p.tile_start[k + 1];
     if (v0 >= v1) return;
@@ -397,18 +414,28 @@ __device__ __forceinline__ void tile_item(const SweepParams &p, int k, const T *
     int *sidx = reinterpret_cast<int *>(smem + (size_t)p.maxe * sizeof(A));
     T *fresh = reinterpret_cast<T *>(smem + (size_t)p.maxe * (sizeof(A) + sizeof(int)));
 
-    // phase A: every in-edge of the tile, four slots per thread per step
+    // phase A: every in-edge of the tile; each thread loads two 16-byte index
+    // vectors before issuing their eight gathers
     const int base = ea & ~3;
     const int span = eb - base;
-    for (int j = threadIdx.x * 4; j < span; j += blockDim.x * 4) {
-        const int4 q = __ldg(reinterpret_cast<const int4 *>(p.row_idx + base + j));
-        const int pos = base + j - ea;
-        const int src[4] = {q.x, q.y, q.z, q.w};
+    const int step = blockDim.x * 4;
+    for (int j0 = threadIdx.x * 4; j0 < span; j0 += 2 * step) {
+        const int j1 = j0 + step;
+        const int4 q0 = __ldg(reinterpret_cast<const int4 *>(p.row_idx + base + j0));
+        int4 q1 = make_int4(0, 0, 0, 0);
+        if (j1 < span) q1 = __ldg(reinterpret_cast<const int4 *>(p.row_idx + base + j1));
+        const int src[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        A got[8];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int sl = pos + c;
+        for (int c = 0; c < 8; ++c) {
+            const int sl = base + (c < 4 ? j0 + c : j1 + c - 4) - ea;
+            got[c] = (sl >= 0 && sl < ne) ? to_a<A>(yin(src[c])) : A(0);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int sl = base + (c < 4 ? j0 + c : j1 + c - 4) - ea;
             if (sl >= 0 && sl < ne) {
-                vals[sl] = edge_term<A, W>(p, ea + sl, to_a<A>(ld_y<T, GS>(yin, src[c])));
+                vals[sl] = edge_term<A, W>(p, ea + sl, got[c]);
                 if constexpr (GS) sidx[sl] = src[c];
             }
         }
@@ -450,19 +477,42 @@ __device__ __forceinline__ void tile_item(const SweepParams &p, int k, const T *
     __syncthreads();  // shared memory is reused by the next item
 }
 
+// Bytes of dynamic shared memory for the staged copy of y[0, stage).
+template <typename T>
+__host__ __device__ constexpr size_t stage_bytes(int stage)
+{
+    return ((size_t)stage * sizeof(T) + 15) & ~(size_t)15;
+}
+
 // Persistent loop: block b takes items b, b + G, b + 2G, ... (G = grid size)
-// in that fixed order, so every block's partial sums are reproducible.
+// in that fixed order, so every block's partial sums are reproducible.  The
+// block first copies the hottest contributions y[0, stage) into shared
+// memory (16-byte loads); for the fused sweep that copy is a snapshot, i.e.
+// those reads may see a value older than the one in y, as any asynchronous
+// read may.
 template <typename T, typename A, bool GS, bool W, typename Fin>
 __device__ __forceinline__ void run_items(const SweepParams &p, const T *yin, Fin &fin)
 {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
+    T *staged = reinterpret_cast<T *>(dyn_smem);
+    const int nst = p.stage;
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(yin);
+        int4 *dst = reinterpret_cast<int4 *>(dyn_smem);
+        const int nvec = (int)(stage_bytes<T>(nst) / 16);
+        for (int i = threadIdx.x; i < nvec; i += blockDim.x)
+            dst[i] = GS ? __ldcg(src + i) : __ldg(src + i);
+        __syncthreads();
+    }
+    Src<T, GS> s{yin, staged, nst};
+    unsigned char *tile_smem = dyn_smem + stage_bytes<T>(nst);
     const int nitems = p.nhubseg + p.ntiles;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         if (item < p.nhubseg) {
-            hub_segment<T, A, GS, W>(p, item, yin, fin);
+            hub_segment<T, A, GS, W>(p, item, s, fin);
             __syncthreads();
         } else {
-            tile_item<T, A, GS, W>(p, item - p.nhubseg, yin, fin, dyn_smem);
+            tile_item<T, A, GS, W>(p, item - p.nhubseg, s, fin, tile_smem);
         }
     }
 }
