@@ -90,16 +90,22 @@ typedef struct {
     int32_t t_hub;     /* in-degree >  t_hub: block per vertex, split into
                           segments of hub_seg in-edges (default 1024,
                           at most 4096) */
-    int32_t hub_seg;   /* in-edges per hub segment (default 4096) */
+    int32_t hub_seg;   /* in-edges per hub segment (default 2048) */
     int32_t tile;      /* work units (in-edges + vertices) per tile of
                           non-hub vertices, staged in shared memory
-                          (default 2048, 256 to 4096) */
+                          (default 1024, 256 to 4096) */
     int32_t deterministic_gs; /* 1: fused sweep in strict input id order on
                                  one warp (reproduces Eq. 9; n <= 65536) */
     int32_t stage_kb;  /* shared memory (KB) per block for a copy of the
                           stored vector's first entries, the most-gathered
                           contributions in the degree-ordered ids (default
-                          64; -1 disables; at most 160) */
+                          0 = off; at most 160) */
+    int32_t wait_limit;/* polls of a copy barrier before a device-side wait
+                          gives up with PR_ERR_TIMEOUT (0: 4M) */
+    int32_t test_stall;/* testing only: 1 makes each block's first wait
+                          also wait on a barrier nothing arrives at, so the
+                          timeout path runs (the solve returns
+                          PR_ERR_TIMEOUT and the device stays usable) */
 } pr_tune;
 
 typedef struct {

@@ -80,7 +80,7 @@ struct SolveState {
     int inner_iter;              // defect correction: sweeps in this inner solve
     int outer_iter;              // defect correction: residual evaluations
     int max_outer;
-    int pad0;
+    int error;                   // set by a block whose bounded wait gave up
     double tau;
     double d;
     double base;      // (1-d)/n
@@ -112,12 +112,17 @@ struct Items {
     int32_t nhubseg = 0;          // items of the hub role
     int32_t ntiles = 0;           // items of the tile role
     int32_t maxe = 0;             // largest in-edge count of a tile
-    int32_t stage_kb = 64;        // shared-memory copy of the hottest sources
+    int32_t stage_kb = 0;         // shared-memory copy of the hottest sources
+    int32_t wait_limit = 0;       // copy-barrier polls before a timeout (0: default)
+    int32_t test_stall = 0;       // testing only: force the timeout path
     Buf hubseg_start;             // [nhub + 1] first segment of each hub
     Buf seg_acc;                  // [nhubseg] double partial sums
     Buf hub_cnt;                  // [nhub] segments finished this sweep
     Buf tile_start;               // [ntiles + 1] first vertex of each tile
-    Buf tile_mid;                 // [ntiles] first thread-per-vertex vertex
+    Buf desc;                     // [nhubseg + ntiles] int4 {v0, v1, ea, eb}:
+                                  // vertices [v0, v1), in-list slots [ea, eb)
+    int32_t idxcap = 0;           // shared-memory slots for one item's in-edges
+    int32_t vcap = 0;             // shared-memory slots for one item's vertices
 };
 
 }  // namespace fpr

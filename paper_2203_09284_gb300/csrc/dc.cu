@@ -48,11 +48,11 @@ struct ResidFin {
     Part<double> pt;
     __device__ ResidFin(const DCParams &q_, const Ctx<double> &c_, float rs)
         : q(q_), c(c_), rscale(rs) {}
-    __device__ __forceinline__ double operator()(int u, double acc)
+    __device__ __forceinline__ double base() const { return c.base; }
+    __device__ __forceinline__ double operator()(int u, double acc, int od, double, double yo,
+                                                 double)
     {
-        const int od = q.p.outdeg[u];
         const bool plain = q.weighted || od == 0;  // stored value is x itself
-        const double yo = __ldg(q.y64 + u);
         const double xold = plain ? yo : yo * static_cast<double>(od);
         const double xnew = c.base + c.d * (c.sig * (acc + c.dt));
         const double r = xnew - c.sig * xold;
@@ -103,10 +103,12 @@ __global__ void __launch_bounds__(SWEEP_BS, 4) k_dc_resid(DCParams q)
     const double err = sx->norm ? resmax : res;
     if (sx->history) sx->history[total - 1] = err;
     const bool conv = err <= sx->tau;
-    const bool go_on = !(conv || sx->outer_iter >= sx->max_outer || total >= sx->max_iter);
+    const int error = *reinterpret_cast<volatile int *>(&sx->error);
+    const bool go_on =
+        !(conv || error || sx->outer_iter >= sx->max_outer || total >= sx->max_iter);
     if (!go_on) {
         sx->done = 1;
-        sx->status = conv ? PR_OK : PR_NOT_CONVERGED;
+        sx->status = error ? error : (conv ? PR_OK : PR_NOT_CONVERGED);
         se->done = 1;
     } else {
         se->iter = 0;
@@ -282,7 +284,7 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
 {
     const int32_t n = g->n;
     PR_TRY(buf_alloc(g, g->xbuf, sizeof(double) * (size_t)n + 64, s));  // 16-byte staged reads
-    PR_TRY(buf_alloc(g, g->rbuf, sizeof(float) * (size_t)n, s));
+    PR_TRY(buf_alloc(g, g->rbuf, sizeof(float) * (size_t)n + 64, s));  // 16-byte widened copies
     const bool gs = o->variant == PR_FUSED_GS;
     const bool fp16 = o->precision == PR_FP16_DC;
     const bool weighted = g->weighted;
@@ -339,8 +341,8 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
                      : reinterpret_cast<const void *>(&k_dc_resid<Te, false>);
     L.f_s = pick_sweep<Te, float>(gs, weighted);
     L.f_u = reinterpret_cast<const void *>(&k_dc_update<Te>);
-    L.smem_r = sweep_smem<double, double>(g, false);
-    L.smem_s = sweep_smem<Te, float>(g, gs);
+    L.smem_r = sweep_smem<double, double>(q.p, false);
+    L.smem_s = sweep_smem<Te, float>(inner, gs);
     L.grid_r = sweep_grid(g, q.p, L.f_r, L.smem_r);
     L.grid_s = sweep_grid(g, inner, L.f_s, L.smem_s);
     L.grid_u = (unsigned)ib;

@@ -128,19 +128,29 @@ __global__ void k_tile_starts(int32_t ntiles, int32_t nhub, int32_t n,
     tile_start[k] = lo;
 }
 
-// First vertex of tile k with in-degree <= t_lo (degrees are non-increasing).
-__global__ void k_tile_mid(int32_t ntiles, const int32_t *__restrict__ col_ptr,
-                           const int32_t *__restrict__ tile_start, int t_lo, int32_t *tile_mid)
+// Item descriptors {v0, v1, ea, eb}: hub segments first (one hub each), then
+// tiles.
+__global__ void k_item_desc(int32_t nhubseg, int32_t nhub, const int32_t *__restrict__ hubseg_start,
+                            int hub_seg, int32_t ntiles, const int32_t *__restrict__ tile_start,
+                            const int32_t *__restrict__ col_ptr, int4 *desc)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ntiles) return;
-    int lo = tile_start[k], hi = tile_start[k + 1];
-    while (lo < hi) {
-        int mid = lo + ((hi - lo) >> 1);
-        if (col_ptr[mid + 1] - col_ptr[mid] <= t_lo) hi = mid;
-        else lo = mid + 1;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nhubseg + ntiles) return;
+    if (i < nhubseg) {
+        int lo = 0, hi = nhub - 1;  // hub owning segment i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (hubseg_start[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const int h = lo;
+        const int a = col_ptr[h] + (i - hubseg_start[h]) * hub_seg;
+        desc[i] = make_int4(h, h + 1, a, min(a + hub_seg, col_ptr[h + 1]));
+    } else {
+        const int k = i - nhubseg;
+        const int v0 = tile_start[k], v1 = tile_start[k + 1];
+        desc[i] = make_int4(v0, v1, col_ptr[v0], col_ptr[v1]);
     }
-    tile_mid[k] = lo;
 }
 
 pr_tune effective_tune(const pr_graph *g, const pr_tune *t)
@@ -153,13 +163,15 @@ pr_tune effective_tune(const pr_graph *g, const pr_tune *t)
         if (t->tile > 0) r.tile = t->tile;
         if (t->stage_kb != 0) r.stage_kb = t->stage_kb;
         r.deterministic_gs = t->deterministic_gs;
+        r.wait_limit = t->wait_limit > 0 ? t->wait_limit : 0;
+        r.test_stall = t->test_stall ? 1 : 0;
     }
     r.stage_kb = r.stage_kb < 0 ? 0 : std::min(r.stage_kb, 160);
     // a tile stages up to tile + t_hub in-edges in shared memory: both are
     // capped at 4096 (at most 128 KB per block for the FP64 fused sweep)
     r.t_hub = std::max(1, std::min(r.t_hub, 4096));
     r.t_lo = std::max(0, std::min(r.t_lo, r.t_hub));
-    r.hub_seg = std::max(256, std::min(r.hub_seg, 1 << 20));
+    r.hub_seg = std::max(256, std::min(r.hub_seg, 8192));
     r.tile = std::max(256, std::min(r.tile, 4096));
     return r;
 }
@@ -175,6 +187,8 @@ pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
 {
     Items &it = g->items;
     it.stage_kb = t.stage_kb;
+    it.wait_limit = t.wait_limit;
+    it.test_stall = t.test_stall;
     if (it.t_lo == t.t_lo && it.t_hub == t.t_hub && it.hub_seg == t.hub_seg &&
         it.tile_c == t.tile)
         return PR_OK;
@@ -221,19 +235,23 @@ pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
     const int64_t work = (int64_t)(ends[1] - ends[0]) + (n - it.nhub);
     it.ntiles = (int32_t)((work + t.tile - 1) / t.tile);
     PR_TRY(buf_alloc(g, it.tile_start, sizeof(int32_t) * (size_t)(it.ntiles + 1), s));
-    PR_TRY(buf_alloc(g, it.tile_mid, sizeof(int32_t) * (size_t)std::max(it.ntiles, 1), s));
     k_tile_starts<<<(it.ntiles + 256) / 256, 256, 0, s>>>(it.ntiles, it.nhub, n, rcp, t.tile,
                                                           it.tile_start.as<int32_t>());
     note_launch();
-    if (it.ntiles > 0) {
-        k_tile_mid<<<(it.ntiles + 255) / 256, 256, 0, s>>>(it.ntiles, rcp,
-                                                           it.tile_start.as<int32_t>(), t.t_lo,
-                                                           it.tile_mid.as<int32_t>());
+    const int nitems = it.nhubseg + it.ntiles;
+    PR_TRY(buf_alloc(g, it.desc, sizeof(int4) * (size_t)std::max(nitems, 1), s));
+    if (nitems > 0) {
+        k_item_desc<<<(nitems + 255) / 256, 256, 0, s>>>(
+            it.nhubseg, it.nhub, it.hubseg_start.as<int32_t>(), t.hub_seg, it.ntiles,
+            it.tile_start.as<int32_t>(), rcp, it.desc.as<int4>());
         note_launch();
     }
     PR_LAUNCH_CHECK();
-    // a tile's in-edges: fewer than tile + (in-degree of its last vertex)
+    // a tile's in-edges: fewer than tile + (in-degree of its last vertex);
+    // shared-memory capacities leave room for 16-byte widening of each range
     it.maxe = (t.tile + t.t_hub + 3) & ~3;
+    it.idxcap = (std::max(it.maxe, t.hub_seg) + 8 + 3) & ~3;
+    it.vcap = (t.tile + 16 + 7) & ~7;
     it.t_lo = t.t_lo;
     it.t_hub = t.t_hub;
     it.hub_seg = t.hub_seg;
@@ -361,13 +379,14 @@ static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, 
                     std::make_pair(&g->inv64, sizeof(double) * (size_t)n),
                     std::make_pair(&g->n2o, sizeof(int32_t) * (size_t)n),
                     std::make_pair(&g->o2n, sizeof(int32_t) * (size_t)n),
-                    std::make_pair(&g->r_outdeg, sizeof(int32_t) * (size_t)n),
-                    std::make_pair(&g->r_col_ptr, sizeof(int32_t) * (size_t)(n + 1)),
-                    // padded so that 16-byte index loads never run past the end
-                    std::make_pair(&g->r_row_idx, sizeof(int32_t) * (mm + 4)),
+                    // the sweep's arrays are padded by 16 entries: its bulk
+                    // copies widen every range to 16-byte boundaries
+                    std::make_pair(&g->r_outdeg, sizeof(int32_t) * ((size_t)n + 16)),
+                    std::make_pair(&g->r_col_ptr, sizeof(int32_t) * ((size_t)n + 17)),
+                    std::make_pair(&g->r_row_idx, sizeof(int32_t) * (mm + 16)),
                     std::make_pair(&g->r_csc_eid, sizeof(int32_t) * mm),
-                    std::make_pair(&g->r_inv64, sizeof(double) * (size_t)n),
-                    std::make_pair(&g->r_inv32, sizeof(float) * (size_t)n),
+                    std::make_pair(&g->r_inv64, sizeof(double) * ((size_t)n + 16)),
+                    std::make_pair(&g->r_inv32, sizeof(float) * ((size_t)n + 16)),
                     std::make_pair(&g->state, 2 * sizeof(SolveState) + 64)})
         PR_TRY(buf_alloc(g, *pb.first, pb.second, s));
     PR_CUDA(cudaMallocHost(&g->host_state, 2 * sizeof(SolveState) + 64));
@@ -375,7 +394,11 @@ static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, 
     PR_CUDA(cudaMemsetAsync(g->outdeg.p, 0, sizeof(int32_t) * n, s));
     PR_CUDA(cudaMemsetAsync(g->indeg.p, 0, sizeof(int32_t) * n, s));
     PR_CUDA(cudaMemsetAsync(flags_dev, 0, 4 * sizeof(int32_t), s));
-    PR_CUDA(cudaMemsetAsync(g->r_row_idx.p, 0, sizeof(int32_t) * (mm + 4), s));
+    PR_CUDA(cudaMemsetAsync(g->r_row_idx.p, 0, sizeof(int32_t) * (mm + 16), s));
+    PR_CUDA(cudaMemsetAsync(g->r_col_ptr.p, 0, sizeof(int32_t) * ((size_t)n + 17), s));
+    PR_CUDA(cudaMemsetAsync(g->r_outdeg.p, 0, sizeof(int32_t) * ((size_t)n + 16), s));
+    PR_CUDA(cudaMemsetAsync(g->r_inv64.p, 0, sizeof(double) * ((size_t)n + 16), s));
+    PR_CUDA(cudaMemsetAsync(g->r_inv32.p, 0, sizeof(float) * ((size_t)n + 16), s));
 
     // 1. degrees (+ id and weight validation)
     if (m > 0) {
@@ -472,8 +495,8 @@ static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, 
         g->weighted = true;
         for (auto pb : {std::make_pair(&g->w, sizeof(float) * (size_t)m),
                         std::make_pair(&g->rowsum, sizeof(double) * (size_t)n),
-                        std::make_pair(&g->p64_csc, sizeof(double) * (size_t)m),
-                        std::make_pair(&g->p32_csc, sizeof(float) * (size_t)m)})
+                        std::make_pair(&g->p64_csc, sizeof(double) * ((size_t)m + 16)),
+                        std::make_pair(&g->p32_csc, sizeof(float) * ((size_t)m + 16))})
             PR_TRY(buf_alloc(g, *pb.first, pb.second, s));
         PR_CUDA(cudaMemcpyAsync(g->w.p, w, sizeof(float) * (size_t)m, cudaMemcpyDeviceToDevice, s));
         k_rowsum<<<(n + 255) / 256, 256, 0, s>>>(n, g->row_ptr.as<int32_t>(),
@@ -527,10 +550,12 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
     }
     g->tune.t_lo = 16;
     g->tune.t_hub = 1024;
-    g->tune.hub_seg = 4096;
-    g->tune.tile = 2048;
+    g->tune.hub_seg = 2048;
+    g->tune.tile = 1024;
     g->tune.deterministic_gs = 0;
-    g->tune.stage_kb = 64;
+    g->tune.stage_kb = 0;
+    g->tune.wait_limit = 0;
+    g->tune.test_stall = 0;
     pr_status st = PR_OK;
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess)

@@ -75,18 +75,19 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem)
     p.outdeg = g->r_outdeg.as<int32_t>();
     p.inv = fp64 ? g->r_inv64.p : g->r_inv32.p;
     p.ew = g->weighted ? (fp64 ? g->p64_csc.p : g->p32_csc.p) : nullptr;
+    p.desc = it.desc.as<int4>();
     p.nhub = it.nhub;
-    p.hubseg_start = it.hubseg_start.as<int32_t>();
     p.nhubseg = it.nhubseg;
-    p.hub_seg = it.hub_seg;
+    p.ntiles = it.ntiles;
+    p.t_lo = it.t_lo;
+    p.hubseg_start = it.hubseg_start.as<int32_t>();
     p.seg_acc = it.seg_acc.as<double>();
     p.hub_cnt = it.hub_cnt.as<int32_t>();
-    p.ntiles = it.ntiles;
-    p.tile_c = it.tile_c;
-    p.maxe = it.maxe;
-    p.tile_start = it.tile_start.as<int32_t>();
-    p.tile_mid = it.tile_mid.as<int32_t>();
+    p.idxcap = it.idxcap;
+    p.vcap = it.vcap;
     p.stage = (int32_t)std::min<int64_t>(g->n, (int64_t)it.stage_kb * 1024 / (int64_t)elem);
+    p.wait_limit = (uint32_t)it.wait_limit;
+    p.test_stall = it.test_stall;
     p.y0 = g->ybuf.p;
     p.y1 = static_cast<char *>(g->ybuf.p) + ((g->n * elem + 255) & ~(size_t)255);
     p.st = g->state.as<SolveState>();
@@ -219,18 +220,16 @@ template const void *pick_sweep<float, float>(bool, bool);
 template const void *pick_sweep<__nv_bfloat16, float>(bool, bool);
 template const void *pick_sweep<__half, float>(bool, bool);
 
+// Dynamic shared memory of a sweep launch with these parameters.
 template <typename T, typename A>
-size_t sweep_smem(const pr_graph *g, bool gs)
+size_t sweep_smem(const SweepParams &p, bool gs)
 {
-    const int stage = (int)std::min<int64_t>(g->n, (int64_t)g->items.stage_kb * 1024 / sizeof(T));
-    return stage_bytes<T>(stage) +
-           (gs ? tile_smem_bytes<T, A, true>(g->items.maxe, g->items.tile_c)
-               : tile_smem_bytes<T, A, false>(g->items.maxe, g->items.tile_c));
+    return gs ? layout_of<T, A, true>(p).total : layout_of<T, A, false>(p).total;
 }
-template size_t sweep_smem<double, double>(const pr_graph *, bool);
-template size_t sweep_smem<float, float>(const pr_graph *, bool);
-template size_t sweep_smem<__nv_bfloat16, float>(const pr_graph *, bool);
-template size_t sweep_smem<__half, float>(const pr_graph *, bool);
+template size_t sweep_smem<double, double>(const SweepParams &, bool);
+template size_t sweep_smem<float, float>(const SweepParams &, bool);
+template size_t sweep_smem<__nv_bfloat16, float>(const SweepParams &, bool);
+template size_t sweep_smem<__half, float>(const SweepParams &, bool);
 
 // Runs the sweep loop for precision T (plain forms).
 template <typename T, typename A>
@@ -275,7 +274,7 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
         block = 32;
     } else {
         func = pick_sweep<T, A>(gs, weighted);
-        smem = sweep_smem<T, A>(g, gs);
+        smem = sweep_smem<T, A>(p, gs);
         grid = sweep_grid(g, p, func, smem);
         block = SWEEP_BS;
     }

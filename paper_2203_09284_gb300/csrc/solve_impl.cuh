@@ -23,6 +23,6 @@ pr_status solve_dc(pr_graph *g, const pr_options *o, const pr_tune &tn, double *
 template <typename T, typename A>
 const void *pick_sweep(bool gs, bool weighted);
 template <typename T, typename A>
-size_t sweep_smem(const pr_graph *g, bool gs);
+size_t sweep_smem(const SweepParams &p, bool gs);
 
 }  // namespace fpr

@@ -7,8 +7,7 @@
 // stop decision (Algorithm 1/2 `while error > threshold`).
 //
 // Everything runs in the degree-ordered numbering (in-degree descending):
-// hubs are the ids [0, nhub), and the most-gathered contributions share
-// cache lines.  Stored vector y (one entry per vertex):
+// hubs are the ids [0, nhub).  Stored vector y (one entry per vertex):
 //   y_u = x~_u * inv_outdeg[u]   if u has out-edges (its contribution, the
 //                                 paper's contributionList entry)
 //   y_u = x~_u                    if u is dangling (never gathered), or for
@@ -16,18 +15,22 @@
 // where the true rank is x_u = sigma * x~_u.  Reading a vertex's own old rank
 // and gathering its in-neighbours touch the same array.
 //
-// Work items, in launch order (heavy first), taken round-robin by a
-// persistent grid:
-//   hub segment  hub_seg in-edges of one hub summed by a block; the block
-//                finishing a hub's last segment adds the segment sums in order
-//                and updates the hub (block per vertex)
+// Work items, in launch order (heavy first), each described by
+// {v0, v1, ea, eb} (vertices [v0, v1), in-list slots [ea, eb)):
+//   hub segment  hub_seg in-edges of one hub (v1 = v0 + 1) summed by a block;
+//                the block finishing a hub's last segment adds the segment
+//                sums in order and updates the hub (block per vertex)
 //   tile         consecutive non-hub vertices with at most `tile` units of
-//                work: all their in-edges are gathered into shared memory with
-//                16-byte index loads (every gather of the tile in flight at
-//                once), then reduced by a warp per vertex (in-degree > t_lo)
-//                or a thread per vertex (in-degree <= t_lo)
-// The per-vertex epilogue is a functor, so the same traversal serves the
-// PageRank sweep, the correction sweep and the FP64 residual sweep of the
+//                work, reduced by a warp per vertex (in-degree > t_lo) or a
+//                thread per vertex (in-degree <= t_lo)
+// A persistent grid takes the items round-robin.  Each block double-buffers
+// them in shared memory: while it works on one item, bulk copies (TMA,
+// cp.async.bulk) bring the next item's contiguous streams -- in-list indices,
+// offsets, out-degrees, 1/outdeg, old stored values, right-hand side, edge
+// weights -- so the only memory latency left on the item's path is the random
+// gather of the in-neighbours' contributions, all of which are in flight at
+// once.  The per-vertex epilogue is a functor, so the same traversal serves
+// the PageRank sweep, the correction sweep and the FP64 residual sweep of the
 // defect-correction forms.
 //
 // Jacobi (Algorithm 1, Eq. 2): reads y[iter & 1], writes the other buffer.
@@ -35,34 +38,35 @@
 // loads and stores, so a vertex sees whichever contribution is there (new if
 // its in-neighbour was already updated in this sweep).  Inside a tile, the
 // vertices are updated warp-vertices first, then thread-vertices in rounds;
-// a later vertex reads the values of the tile's earlier vertices from shared
-// memory.  After each fused sweep the iterate is rescaled to sum 1 by
+// a later vertex reads the new values of the tile's earlier vertices from
+// shared memory.  After each fused sweep the iterate is rescaled to sum 1 by
 // folding 1/sum into sigma.
 #pragma once
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace fpr {
 
 constexpr int SWEEP_BS = 256;
+constexpr uint32_t DEFAULT_WAIT_LIMIT = 1u << 22;
 
 struct SweepParams {
     int32_t n;
-    const int32_t *__restrict__ col_ptr;  // relabelled in-lists
-    const int32_t *__restrict__ row_idx;  // (padded by 4 entries)
+    const int32_t *__restrict__ col_ptr;  // relabelled in-lists (padded)
+    const int32_t *__restrict__ row_idx;
     const int32_t *__restrict__ outdeg;
     const void *inv;              // A[n]: 1/outdeg in the arithmetic type
     const void *ew;               // A[m]: P per in-list slot (weighted) or null
-    int32_t nhub;
+    const int4 *desc;             // [nhubseg + ntiles] item descriptors
+    int32_t nhub, nhubseg, ntiles, t_lo;
     const int32_t *hubseg_start;  // [nhub + 1]
-    int32_t nhubseg, hub_seg;
     double *seg_acc;              // [nhubseg]
     int32_t *hub_cnt;             // [nhub]
-    int32_t ntiles, tile_c, maxe;
-    const int32_t *tile_start;    // [ntiles + 1]
-    const int32_t *tile_mid;      // [ntiles]
-    int32_t stage;                // y[0, stage) is copied to shared memory at
-                                  // the start of the sweep (hottest sources)
+    int32_t idxcap, vcap;         // shared-memory capacity of one item
+    int32_t stage;                // y[0, stage) is copied to shared memory
+    uint32_t wait_limit;
+    int32_t test_stall;
     void *y0, *y1;                // stored vectors
     const void *rhs;              // A[n] right-hand side, or null: (1-d)/n
     SolveState *st;
@@ -157,35 +161,24 @@ __device__ __forceinline__ Ctx<A> load_ctx(const SolveState *st)
     return c;
 }
 
-// gathered term of in-list slot i whose source holds `val`
-template <typename A, bool W>
-__device__ __forceinline__ A edge_term(const SweepParams &p, int i, A val)
-{
-    if constexpr (W) return static_cast<const A *>(p.ew)[i] * val;
-    else return val;
-}
-
 // Epilogue of the PageRank (or correction) sweep: new value of vertex u from
-// its gathered sum `acc` (stored units); returns the stored value written.
+// its gathered sum `acc` (stored units), its out-degree, 1/outdeg, old stored
+// value and right-hand side; returns the stored value written.
 template <typename T, typename A, bool GS, bool W>
 struct SweepFin {
     const SweepParams &p;
     Ctx<A> c;
-    const T *yin;
     T *yout;
     Part<A> pt;
-    __device__ SweepFin(const SweepParams &p_, const Ctx<A> &c_, const T *yi, T *yo)
-        : p(p_), c(c_), yin(yi), yout(yo) {}
-    __device__ __forceinline__ T operator()(int u, A acc)
+    __device__ SweepFin(const SweepParams &p_, const Ctx<A> &c_, T *yo) : p(p_), c(c_), yout(yo) {}
+    __device__ __forceinline__ A base() const { return c.base; }
+    __device__ __forceinline__ T operator()(int u, A acc, int od, A inv, T yold, A r)
     {
-        const int od = p.outdeg[u];
-        const A yo = to_a<A>(ld_y<T, GS>(yin, u));
+        const A yo = to_a<A>(yold);
         const A xold = (W || od == 0) ? yo : yo * static_cast<A>(od);  // stored units
-        const A r = p.rhs ? static_cast<const A *>(p.rhs)[u] : c.base;
         const A xnew = r + c.d * (c.sig * (acc + c.dt));                 // true units
         const A diff = aabs(xnew - c.sig * xold);
         const A xs = xnew * c.rsig;                                       // stored units
-        const A inv = static_cast<const A *>(p.inv)[u];
         const T yn = from_a<T>((W || od == 0) ? xs : xs * inv);
         st_y<T, GS>(yout, u, yn);
         pt.l1 += diff;
@@ -195,46 +188,6 @@ struct SweepFin {
         return yn;
     }
 };
-
-// Where a gathered contribution comes from: the copy of y[0, nstaged) in
-// shared memory (the hottest sources in the degree-ordered ids), else y.
-template <typename T, bool GS>
-struct Src {
-    const T *y;
-    const T *staged;
-    int nstaged;
-    __device__ __forceinline__ T operator()(int v) const
-    {
-        return v < nstaged ? staged[v] : ld_y<T, GS>(y, v);
-    }
-};
-
-// Sum over in-list slots [a, b) by one warp, 16-byte index loads in the body.
-template <typename T, typename A, bool GS, bool W>
-__device__ __forceinline__ A warp_gather(const SweepParams &p, const Src<T, GS> &y, int a, int b,
-                                         int lane)
-{
-    const int32_t *__restrict__ row_idx = p.row_idx;
-    A acc = 0;
-    if (b - a < 64) {
-        for (int i = a + lane; i < b; i += 32)
-            acc += edge_term<A, W>(p, i, to_a<A>(y(row_idx[i])));
-        return acc;
-    }
-    const int a4 = (a + 3) & ~3;
-    const int b4 = b & ~3;
-    if (lane < a4 - a) acc += edge_term<A, W>(p, a + lane, to_a<A>(y(row_idx[a + lane])));
-    for (int i = a4 + 4 * lane; i < b4; i += 128) {
-        const int4 q = __ldg(reinterpret_cast<const int4 *>(row_idx + i));
-        const A s0 = edge_term<A, W>(p, i, to_a<A>(y(q.x)));
-        const A s1 = edge_term<A, W>(p, i + 1, to_a<A>(y(q.y)));
-        const A s2 = edge_term<A, W>(p, i + 2, to_a<A>(y(q.z)));
-        const A s3 = edge_term<A, W>(p, i + 3, to_a<A>(y(q.w)));
-        acc += (s0 + s1) + (s2 + s3);
-    }
-    if (lane < b - b4) acc += edge_term<A, W>(p, b4 + lane, to_a<A>(y(row_idx[b4 + lane])));
-    return acc;
-}
 
 // Reduces the block's partial sums and adds them to the sweep accumulators.
 template <typename A>
@@ -307,7 +260,8 @@ __device__ __forceinline__ void take_sums(SolveState *st, double &res, double &r
 }
 
 // Closes a PageRank sweep (dc == 0) or a correction sweep (dc != 0): next
-// scalars, history, stop test, loop condition.
+// scalars, history, stop test, loop condition.  A device-side error ends the
+// loop with that status.
 __device__ __forceinline__ void close_sweep(const SweepParams &p)
 {
     SolveState *st = p.st;
@@ -322,11 +276,12 @@ __device__ __forceinline__ void close_sweep(const SweepParams &p)
     if (p.renorm && sum > 0) st->sigma = 1.0 / sum;
     const double err = st->norm ? resmax : res;
     bool stop, conv;
+    const int error = *reinterpret_cast<volatile int *>(&st->error);
     if (!p.dc) {
         if (st->history) st->history[it - 1] = err;
         conv = err <= st->tau;
-        stop = conv || it >= st->max_iter;
-        st->status = conv ? PR_OK : PR_NOT_CONVERGED;
+        stop = conv || it >= st->max_iter || error;
+        st->status = error ? error : (conv ? PR_OK : PR_NOT_CONVERGED);
     } else {
         SolveState *so = p.st_outer;
         const int total = so->iter + 1;
@@ -334,187 +289,280 @@ __device__ __forceinline__ void close_sweep(const SweepParams &p)
         st->inner_iter += 1;
         if (so->history) so->history[total - 1] = err;
         conv = err <= st->tau;
-        stop = conv || it >= st->max_iter || total >= so->max_iter;
+        stop = conv || it >= st->max_iter || total >= so->max_iter || error;
+        if (error) {
+            so->error = error;
+            so->status = error;
+            so->done = 1;
+        }
     }
     st->done = stop ? 1 : 0;
     __threadfence();
     if (p.use_cond) cudaGraphSetConditional(p.cond, stop ? 0u : 1u);
 }
 
-// Hub segment b: a block sums hub_seg in-edges of hub h; the block that
-// completes the hub's last segment adds the segment sums in order and calls
-// the epilogue (thread 0).
-template <typename T, typename A, bool GS, bool W, typename Fin>
-__device__ __forceinline__ void hub_segment(const SweepParams &p, int b, const Src<T, GS> &yin,
-                                            Fin &fin)
+// ------------------------------------------------------- shared memory
+__host__ __device__ constexpr uint32_t a16(size_t b) { return (uint32_t)((b + 15) & ~(size_t)15); }
+
+// Layout of the dynamic shared memory of a sweep block:
+//   [staged y[0, stage)] [item buffer 0] [item buffer 1] [gathered terms]
+//   [fused sweep: slot sources, new tile values] [barriers]
+// and of one item buffer:
+//   [descriptor int4] [indices] [offsets] [out-degrees] [1/outdeg]
+//   [old stored values] [right-hand side] [edge weights]
+struct Layout {
+    uint32_t idx, cp, od, inv, yo, rhs, ew, buf;          // within a buffer
+    uint32_t buf0, buf1, vals, sidx, fresh, bars, total;  // within the block
+};
+
+__host__ __device__ inline Layout make_layout(int idxcap, int vcap, int sa, int st, bool rhs,
+                                              bool w, bool gs, int stage)
 {
-    __shared__ double red[SWEEP_BS / 32];
-    __shared__ int sh_h;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = p.nhub - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (p.hubseg_start[mid] <= b) lo = mid;
-            else hi = mid - 1;
-        }
-        sh_h = lo;
-    }
-    __syncthreads();
-    const int h = sh_h;  // hub vertex id (hubs are the first ids)
-    const int s0 = p.hubseg_start[h];
-    const int nseg = p.hubseg_start[h + 1] - s0;
-    const int k = b - s0;
-    const int a = p.col_ptr[h] + k * p.hub_seg;
-    const int e = min(a + p.hub_seg, p.col_ptr[h + 1]);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    const int per = (((e - a) + nw - 1) / nw + 3) & ~3;
-    const int wa = min(e, a + warp * per), wb = min(e, wa + per);
-    A acc = warp_gather<T, A, GS, W>(p, yin, wa, wb, lane);
-    double s = warp_sum(static_cast<double>(acc));
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot = 0;
-        for (int w = 0; w < nw; ++w) tot += red[w];
-        p.seg_acc[b] = tot;
-        __threadfence();
-        const int done = atomicAdd(&p.hub_cnt[h], 1);
-        if (done == nseg - 1) {
-            __threadfence();
-            const volatile double *sa = p.seg_acc;
-            double all = 0;
-            for (int j = 0; j < nseg; ++j) all += sa[s0 + j];
-            p.hub_cnt[h] = 0;
-            fin(h, static_cast<A>(all));
-        }
-    }
+    Layout L;
+    L.idx = 16;
+    L.cp = L.idx + a16((size_t)idxcap * 4);
+    L.od = L.cp + a16((size_t)vcap * 4);
+    L.inv = L.od + a16((size_t)vcap * 4);
+    L.yo = L.inv + a16((size_t)vcap * sa);
+    L.rhs = L.yo + a16((size_t)vcap * st);
+    L.ew = L.rhs + (rhs ? a16((size_t)vcap * sa) : 0);
+    L.buf = L.ew + (w ? a16((size_t)idxcap * sa) : 0);
+    L.buf0 = a16((size_t)stage * st);
+    L.buf1 = L.buf0 + L.buf;
+    L.vals = L.buf1 + L.buf;
+    L.sidx = L.vals + a16((size_t)idxcap * sa);
+    L.fresh = L.sidx + (gs ? a16((size_t)idxcap * 4) : 0);
+    L.bars = L.fresh + (gs ? a16((size_t)vcap * st) : 0);
+    L.total = L.bars + 32;  // three 8-byte barriers
+    return L;
 }
 
-// Shared memory of a tile: gathered terms [maxe] (A); for the fused sweep
-// also the source of each slot [maxe] (int) and the tile's new stored
-// values [tile_c] (T).
 template <typename T, typename A, bool GS>
-__host__ __device__ constexpr size_t tile_smem_bytes(int maxe, int tile_c)
+__host__ __device__ inline Layout layout_of(const SweepParams &p)
 {
-    return GS ? (size_t)maxe * sizeof(A) + (size_t)maxe * sizeof(int) + (size_t)tile_c * sizeof(T) + 64
-              : (size_t)maxe * sizeof(A) + 16;
+    return make_layout(p.idxcap, p.vcap, sizeof(A), sizeof(T), p.rhs != nullptr, p.ew != nullptr,
+                       GS, p.stage);
 }
 
-template <typename T, typename A, bool GS, bool W, typename Fin>
-__device__ __forceinline__ void tile_item(const SweepParams &p, int k, const Src<T, GS> &yin,
-                                          Fin &fin, unsigned char *smem)
-{
-    const int v0 = p.tile_start[k], v1 = p.tile_start[k + 1];
-    if (v0 >= v1) return;
-    const int vm = p.tile_mid[k];
-    const int ea = p.col_ptr[v0], eb = p.col_ptr[v1];
-    const int ne = eb - ea;
-    A *vals = reinterpret_cast<A *>(smem);
-    int *sidx = reinterpret_cast<int *>(smem + (size_t)p.maxe * sizeof(A));
-    T *fresh = reinterpret_cast<T *>(smem + (size_t)p.maxe * (sizeof(A) + sizeof(int)));
+// Where a gathered contribution comes from: the copy of y[0, nstaged) in
+// shared memory (the hottest sources in the degree-ordered ids), else y.
+template <typename T, bool GS>
+struct Src {
+    const T *y;
+    const T *staged;
+    int nstaged;
+    __device__ __forceinline__ T operator()(int v) const
+    {
+        return v < nstaged ? staged[v] : ld_y<T, GS>(y, v);
+    }
+};
 
-    // phase A: every in-edge of the tile; each thread loads two 16-byte index
-    // vectors before issuing their eight gathers
-    const int base = ea & ~3;
-    const int span = eb - base;
-    const int step = blockDim.x * 4;
-    for (int j0 = threadIdx.x * 4; j0 < span; j0 += 2 * step) {
-        const int j1 = j0 + step;
-        const int4 q0 = __ldg(reinterpret_cast<const int4 *>(p.row_idx + base + j0));
-        int4 q1 = make_int4(0, 0, 0, 0);
-        if (j1 < span) q1 = __ldg(reinterpret_cast<const int4 *>(p.row_idx + base + j1));
-        const int src[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-        A got[8];
+// Thread 0: bulk copies of item `item` into `buf`, completing on `bar`.
+// Ranges are widened to 16-byte boundaries (the arrays are padded for it).
+template <typename T, typename A>
+__device__ __forceinline__ void issue_item(const SweepParams &p, const Layout &L, int item,
+                                           unsigned char *buf, uint64_t *bar, const T *yin)
+{
+    const int4 d = __ldg(p.desc + item);
+    *reinterpret_cast<int4 *>(buf) = d;
+    const int v0 = d.x, v1 = d.y, ea = d.z, eb = d.w;
+    // pass 0 sums the bytes announced on the barrier, pass 1 issues the copies
+    uint32_t tx = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) mbar_expect_tx(bar, tx);
+        auto range = [&](uint32_t off, const void *base, int elem, int lo, int hi) {
+            const int al = 16 / elem;
+            const int s = lo & ~(al - 1), e = (hi + al - 1) & ~(al - 1);
+            if (e <= s) return;
+            const uint32_t bytes = (uint32_t)(e - s) * (uint32_t)elem;
+            if (pass == 0) tx += bytes;
+            else bulk_load(buf + off, static_cast<const char *>(base) + (size_t)s * elem, bytes, bar);
+        };
+        range(L.idx, p.row_idx, 4, ea, eb);
+        range(L.cp, p.col_ptr, 4, v0, v1 + 1);
+        range(L.od, p.outdeg, 4, v0, v1);
+        range(L.inv, p.inv, sizeof(A), v0, v1);
+        range(L.yo, yin, sizeof(T), v0, v1);
+        if (p.rhs) range(L.rhs, p.rhs, sizeof(A), v0, v1);
+        if (p.ew) range(L.ew, p.ew, sizeof(A), ea, eb);
+    }
+}
+
+// Works on one item whose streams are in `buf`.
+template <typename T, typename A, bool GS, bool W, typename Fin>
+__device__ __forceinline__ void do_item(const SweepParams &p, const Layout &L, int item,
+                                        const unsigned char *buf, unsigned char *smem,
+                                        const Src<T, GS> &src, Fin &fin)
+{
+    __shared__ double hub_red[SWEEP_BS / 32];
+    const int4 d = *reinterpret_cast<const int4 *>(buf);
+    const int v0 = d.x, v1 = d.y, ea = d.z, eb = d.w;
+    const int ne = eb - ea;
+    constexpr int alA = 16 / sizeof(A), alT = 16 / sizeof(T);
+    const int *idx = reinterpret_cast<const int *>(buf + L.idx) - (ea & ~3);
+    const int *cp = reinterpret_cast<const int *>(buf + L.cp) - (v0 & ~3);
+    const int *od = reinterpret_cast<const int *>(buf + L.od) - (v0 & ~3);
+    const A *inv = reinterpret_cast<const A *>(buf + L.inv) - (v0 & ~(alA - 1));
+    const T *yo = reinterpret_cast<const T *>(buf + L.yo) - (v0 & ~(alT - 1));
+    const A *rhs = reinterpret_cast<const A *>(buf + L.rhs) - (v0 & ~(alA - 1));
+    const A *ew = reinterpret_cast<const A *>(buf + L.ew) - (ea & ~(alA - 1));
+    A *vals = reinterpret_cast<A *>(smem + L.vals);
+    int *sidx = reinterpret_cast<int *>(smem + L.sidx);
+    T *fresh = reinterpret_cast<T *>(smem + L.fresh);
+    const bool has_rhs = p.rhs != nullptr;
+
+    // phase A: every in-edge, four independent gathers per thread per step
+    for (int s0 = threadIdx.x; s0 < ne; s0 += 4 * SWEEP_BS) {
+        int v[4];
+        A got[4];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int sl = base + (c < 4 ? j0 + c : j1 + c - 4) - ea;
-            got[c] = (sl >= 0 && sl < ne) ? to_a<A>(yin(src[c])) : A(0);
+        for (int c = 0; c < 4; ++c) {
+            const int s = s0 + c * SWEEP_BS;
+            v[c] = s < ne ? idx[ea + s] : 0;
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int sl = base + (c < 4 ? j0 + c : j1 + c - 4) - ea;
-            if (sl >= 0 && sl < ne) {
-                vals[sl] = edge_term<A, W>(p, ea + sl, got[c]);
-                if constexpr (GS) sidx[sl] = src[c];
+        for (int c = 0; c < 4; ++c) {
+            const int s = s0 + c * SWEEP_BS;
+            got[c] = s < ne ? to_a<A>(src(v[c])) : A(0);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int s = s0 + c * SWEEP_BS;
+            if (s < ne) {
+                vals[s] = W ? ew[ea + s] * got[c] : got[c];
+                if constexpr (GS) sidx[s] = v[c];
             }
         }
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // phase B1: in-degree > t_lo (the tile's first vertices): warp per vertex
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = SWEEP_BS / 32;
+
+    if (v0 < p.nhub) {
+        // hub segment: block sum, then the hub's last segment finishes it
+        double s = 0;
+        for (int i = threadIdx.x; i < ne; i += SWEEP_BS) s += static_cast<double>(vals[i]);
+        s = warp_sum(s);
+        if (lane == 0) hub_red[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0;
+            for (int w = 0; w < nw; ++w) tot += hub_red[w];
+            const int h = v0;
+            p.seg_acc[item] = tot;
+            __threadfence();
+            const int s0 = p.hubseg_start[h];
+            const int nseg = p.hubseg_start[h + 1] - s0;
+            if (atomicAdd(&p.hub_cnt[h], 1) == nseg - 1) {
+                __threadfence();
+                const volatile double *sa = p.seg_acc;
+                double all = 0;
+                for (int j = 0; j < nseg; ++j) all += sa[s0 + j];
+                p.hub_cnt[h] = 0;
+                fin(h, static_cast<A>(all), od[h], inv[h], yo[h], has_rhs ? rhs[h] : fin.base());
+            }
+        }
+        return;
+    }
+
+    // tile: first vertex with in-degree <= t_lo (degrees are non-increasing)
+    int vm;
+    {
+        int lo = v0, hi = v1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cp[mid + 1] - cp[mid] <= p.t_lo) hi = mid;
+            else lo = mid + 1;
+        }
+        vm = lo;
+    }
+    // phase B1: in-degree > t_lo: warp per vertex
     for (int u = v0 + warp; u < vm; u += nw) {
-        const int a = p.col_ptr[u] - ea, e = p.col_ptr[u + 1] - ea;
+        const int a = cp[u] - ea, e = cp[u + 1] - ea;
         A acc = 0;
         for (int i = a + lane; i < e; i += 32) acc += vals[i];
         acc = warp_sum(acc);
         if (lane == 0) {
-            const T yn = fin(u, acc);
+            const T yn = fin(u, acc, od[u], inv[u], yo[u], has_rhs ? rhs[u] : fin.base());
             if constexpr (GS) fresh[u - v0] = yn;
         }
     }
     if constexpr (GS) __syncthreads();
-    // phase B2: thread per vertex, in rounds of blockDim
-    for (int u0 = vm; u0 < v1; u0 += blockDim.x) {
+    // phase B2: thread per vertex, in rounds of the block size
+    for (int u0 = vm; u0 < v1; u0 += SWEEP_BS) {
         const int u = u0 + threadIdx.x;
         if (u < v1) {
-            const int a = p.col_ptr[u] - ea, e = p.col_ptr[u + 1] - ea;
+            const int a = cp[u] - ea, e = cp[u + 1] - ea;
             A acc = 0;
             for (int i = a; i < e; ++i) {
                 A val = vals[i];
                 if constexpr (GS) {
-                    // in-tile source already updated in this sweep: fresh value
+                    // in-tile source already updated in this sweep: new value
                     const int v = sidx[i];
-                    if (v >= v0 && v < u0) val = edge_term<A, W>(p, ea + i, to_a<A>(fresh[v - v0]));
+                    if (v >= v0 && v < u0) {
+                        const A nv = to_a<A>(fresh[v - v0]);
+                        val = W ? ew[ea + i] * nv : nv;
+                    }
                 }
                 acc += val;
             }
-            const T yn = fin(u, acc);
+            const T yn = fin(u, acc, od[u], inv[u], yo[u], has_rhs ? rhs[u] : fin.base());
             if constexpr (GS) fresh[u - v0] = yn;
         }
         if constexpr (GS) __syncthreads();
     }
-    __syncthreads();  // shared memory is reused by the next item
 }
 
-// Bytes of dynamic shared memory for the staged copy of y[0, stage).
-template <typename T>
-__host__ __device__ constexpr size_t stage_bytes(int stage)
-{
-    return ((size_t)stage * sizeof(T) + 15) & ~(size_t)15;
-}
-
-// Persistent loop: block b takes items b, b + G, b + 2G, ... (G = grid size)
-// in that fixed order, so every block's partial sums are reproducible.  The
-// block first copies the hottest contributions y[0, stage) into shared
-// memory (16-byte loads); for the fused sweep that copy is a snapshot, i.e.
-// those reads may see a value older than the one in y, as any asynchronous
-// read may.
+// Persistent, double-buffered loop over the items of this block (items
+// blockIdx, blockIdx + G, ... in that fixed order, so every block's partial
+// sums are reproducible).  Returns false if a copy wait gave up.
 template <typename T, typename A, bool GS, bool W, typename Fin>
 __device__ __forceinline__ void run_items(const SweepParams &p, const T *yin, Fin &fin)
 {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    T *staged = reinterpret_cast<T *>(dyn_smem);
-    const int nst = p.stage;
-    {
-        const int4 *src = reinterpret_cast<const int4 *>(yin);
-        int4 *dst = reinterpret_cast<int4 *>(dyn_smem);
-        const int nvec = (int)(stage_bytes<T>(nst) / 16);
-        for (int i = threadIdx.x; i < nvec; i += blockDim.x)
-            dst[i] = GS ? __ldcg(src + i) : __ldg(src + i);
-        __syncthreads();
-    }
-    Src<T, GS> s{yin, staged, nst};
-    unsigned char *tile_smem = dyn_smem + stage_bytes<T>(nst);
+    const Layout L = layout_of<T, A, GS>(p);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(dyn_smem + L.bars);
+    unsigned char *const buf0 = dyn_smem + L.buf0, *const buf1 = dyn_smem + L.buf1;
     const int nitems = p.nhubseg + p.ntiles;
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-        if (item < p.nhubseg) {
-            hub_segment<T, A, GS, W>(p, item, s, fin);
-            __syncthreads();
-        } else {
-            tile_item<T, A, GS, W>(p, item - p.nhubseg, s, fin, tile_smem);
-        }
+    const uint32_t limit = p.wait_limit ? p.wait_limit : DEFAULT_WAIT_LIMIT;
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);  // nothing ever arrives here (timeout test)
+        mbar_init_fence();
     }
+    // staged copy of the hottest contributions (snapshot for the fused sweep)
+    if (p.stage > 0) {
+        const int4 *s = reinterpret_cast<const int4 *>(yin);
+        int4 *dst = reinterpret_cast<int4 *>(dyn_smem);
+        const int nvec = (int)(a16((size_t)p.stage * sizeof(T)) / 16);
+        for (int i = threadIdx.x; i < nvec; i += SWEEP_BS) dst[i] = GS ? __ldcg(s + i) : __ldg(s + i);
+    }
+    __syncthreads();
+    const Src<T, GS> src{yin, reinterpret_cast<const T *>(dyn_smem), p.stage};
+    if (threadIdx.x == 0 && (int)blockIdx.x < nitems)
+        issue_item<T, A>(p, L, blockIdx.x, buf0, &bars[0], yin);
+    int k = 0;
+    bool timed_out = false;
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++k) {
+        const int b = k & 1;
+        const int next = item + gridDim.x;
+        if (threadIdx.x == 0 && next < nitems) {
+            fence_async_smem();  // generic reads of that buffer precede the copy
+            issue_item<T, A>(p, L, next, b ? buf0 : buf1, &bars[b ^ 1], yin);
+        }
+        bool ok = mbar_wait(&bars[b], (k >> 1) & 1, limit);
+        if (p.test_stall && k == 0) ok = ok && mbar_wait(&bars[2], 0, limit);
+        if (__syncthreads_or(!ok)) {
+            // drain this block's copies still in flight, then report
+            mbar_wait(&bars[b], (k >> 1) & 1, limit);
+            if (next < nitems) mbar_wait(&bars[b ^ 1], ((k + 1) >> 1) & 1, limit);
+            timed_out = true;
+            break;
+        }
+        do_item<T, A, GS, W>(p, L, item, b ? buf1 : buf0, dyn_smem, src, fin);
+        __syncthreads();  // the buffer and the gathered terms are reused
+    }
+    if (timed_out && threadIdx.x == 0) atomicCAS(&p.st->error, 0, (int)PR_ERR_TIMEOUT);
 }
 
 template <typename T, typename A, bool GS, bool W>
@@ -535,7 +583,7 @@ __global__ void __launch_bounds__(SWEEP_BS, 4) k_sweep(SweepParams p)
         yin = static_cast<const T *>((iter & 1) ? p.y1 : p.y0);
         yout = static_cast<T *>((iter & 1) ? p.y0 : p.y1);
     }
-    SweepFin<T, A, GS, W> fin(p, load_ctx<A>(st), yin, yout);
+    SweepFin<T, A, GS, W> fin(p, load_ctx<A>(st), yout);
     run_items<T, A, GS, W>(p, yin, fin);
     block_partials<A>(st, fin.pt);
     if (last_block(st) && threadIdx.x == 0) close_sweep(p);
@@ -553,14 +601,17 @@ __global__ void k_sweep_serial(SweepParams p)
         return;
     }
     T *y = static_cast<T *>(p.y0);
-    SweepFin<T, A, true, false> fin(p, load_ctx<A>(st), y, y);
+    SweepFin<T, A, true, false> fin(p, load_ctx<A>(st), y);
+    const A *inv = static_cast<const A *>(p.inv);
+    const A *rhs = static_cast<const A *>(p.rhs);
     const int lane = threadIdx.x & 31;
     for (int u = 0; u < p.n; ++u) {
         const int a = p.col_ptr[u], e = p.col_ptr[u + 1];
         A acc = 0;
         for (int i = a + lane; i < e; i += 32) acc += to_a<A>(ld_y<T, true>(y, p.row_idx[i]));
         acc = warp_sum(acc);
-        if (lane == 0) fin(u, acc);
+        if (lane == 0)
+            fin(u, acc, p.outdeg[u], inv[u], ld_y<T, true>(y, u), rhs ? rhs[u] : fin.base());
         __syncwarp();
     }
     block_partials<A>(st, fin.pt);

@@ -164,6 +164,22 @@ def test_bin_thresholds_do_not_change_the_result(s16, tune):
     assert l1(x, star.x) <= BOUND
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_dc"])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_device_wait_timeout_is_reported(s16, precision, use_graph):
+    """A copy-barrier wait that runs out (each block's first wait also waits on
+    a barrier nothing arrives at) ends the solve with PR_ERR_TIMEOUT; the
+    device stays usable."""
+    import paper_2203_09284_gb300 as fp
+    n, src, dst, og, g, star = s16
+    with pytest.raises(fp.PageRankError) as e:
+        g.solve(precision=precision, threshold=1e-10, use_graph=use_graph,
+                tune={"test_stall": 1, "wait_limit": 256})
+    assert e.value.status == fp.PR_ERR_TIMEOUT
+    x, r = g.solve(precision=precision, threshold=1e-10, use_graph=use_graph)
+    assert r.status == 0 and l1(x, star.x) <= 1e-10 / (1 - D)
+
+
 def test_ragged_sizes():
     for n_extra in (1, 255, 257, 4097):
         n0, src, dst = gen.rmat(11, 12, seed=n_extra)
