@@ -345,6 +345,7 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     L.smem_s = sweep_smem<Te, float>(inner, gs);
     L.grid_r = sweep_grid(g, q.p, L.f_r, L.smem_r);
     L.grid_s = sweep_grid(g, inner, L.f_s, L.smem_s);
+    if (L.grid_r == 0 || L.grid_s == 0) return PR_ERR_INVALID_ARG;
     L.grid_u = (unsigned)ib;
     bool graph_loop = false;
     if (o->use_graph) {

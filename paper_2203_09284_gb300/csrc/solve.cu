@@ -98,6 +98,14 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem)
 unsigned sweep_grid(const pr_graph *g, const SweepParams &p, const void *func, size_t smem)
 {
     const int nitems = p.nhubseg + p.ntiles;
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
+    if (smem > (size_t)max_smem) {
+        set_error("the tile and hub sizes need %zu bytes of shared memory per block (limit %d): "
+                  "use a smaller tile, t_hub, hub_seg or stage_kb",
+                  smem, max_smem);
+        return 0;
+    }
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
@@ -276,6 +284,7 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
         func = pick_sweep<T, A>(gs, weighted);
         smem = sweep_smem<T, A>(p, gs);
         grid = sweep_grid(g, p, func, smem);
+        if (grid == 0) return PR_ERR_INVALID_ARG;
         block = SWEEP_BS;
     }
     bool graph_loop = false;

@@ -150,7 +150,7 @@ def test_closed_forms_on_gpu(gs):
 
 
 @pytest.mark.parametrize("tune", [{"t_lo": 2, "t_hub": 16, "hub_seg": 256, "tile": 256},
-                                  {"t_lo": 32, "t_hub": 100000, "tile": 8192, "stage_kb": 160},
+                                  {"t_lo": 32, "t_hub": 2048, "tile": 2048, "stage_kb": 16},
                                   {"t_lo": 1, "t_hub": 1, "hub_seg": 512, "tile": 300,
                                    "stage_kb": -1},
                                   {"t_lo": 64, "t_hub": 4096, "hub_seg": 1024, "tile": 1024,
