@@ -349,8 +349,8 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     L.grid_u = (unsigned)ib;
     bool graph_loop = false;
     if (o->use_graph) {
-        const int key = 16 | (gs ? 2 : 0) | (weighted ? 8 : 0) | ((int)o->precision << 8) |
-                        (g->items.stage_kb << 16);
+        const int key = 16 | (gs ? 2 : 0) | (weighted ? 8 : 0) | (g->items.test_stall ? 32 : 0) |
+                        ((int)o->precision << 8) | (g->items.stage_kb << 16);
         cudaGraphExec_t exec;
         PR_TRY(dc_graph(g, key, q, inner, L, &exec));
         PR_CUDA(cudaGraphLaunch(exec, s));

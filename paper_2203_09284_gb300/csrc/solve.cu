@@ -290,7 +290,7 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
     bool graph_loop = false;
     if (o->use_graph) {
         const int key = (fp64 ? 1 : 0) | (gs ? 2 : 0) | (serial ? 4 : 0) | (weighted ? 8 : 0) |
-                        (g->items.stage_kb << 16);
+                        (g->items.test_stall ? 32 : 0) | (g->items.stage_kb << 16);
         cudaGraphExec_t exec;
         PR_TRY(loop_graph(g, key, func, grid, block, smem, p, &exec));
         PR_CUDA(cudaGraphLaunch(exec, s));
@@ -329,8 +329,9 @@ pr_status prepare_solve(pr_graph *g, const pr_options *o, pr_tune &tn, cudaStrea
     tn = effective_tune(g, o->tune);
     const Items &it = g->items;
     if (it.t_lo != tn.t_lo || it.t_hub != tn.t_hub || it.hub_seg != tn.hub_seg ||
-        it.tile_c != tn.tile)
-        release_graphs(g);  // cached loops hold the old work items
+        it.tile_c != tn.tile || it.stage_kb != tn.stage_kb || it.wait_limit != tn.wait_limit ||
+        it.test_stall != tn.test_stall)
+        release_graphs(g);  // cached loops hold the old launch parameters
     PR_TRY(ensure_items(g, tn, s));
     PR_TRY(ensure_workspace(g, s));
     return PR_OK;

@@ -357,13 +357,13 @@ struct Src {
     }
 };
 
-// Thread 0: bulk copies of item `item` into `buf`, completing on `bar`.
-// Ranges are widened to 16-byte boundaries (the arrays are padded for it).
+// Thread 0: bulk copies of the item with descriptor d into `buf`, completing
+// on `bar`.  Ranges are widened to 16-byte boundaries (the arrays are padded
+// for it).
 template <typename T, typename A>
-__device__ __forceinline__ void issue_item(const SweepParams &p, const Layout &L, int item,
+__device__ __forceinline__ void issue_item(const SweepParams &p, const Layout &L, int4 d,
                                            unsigned char *buf, uint64_t *bar, const T *yin)
 {
-    const int4 d = __ldg(p.desc + item);
     *reinterpret_cast<int4 *>(buf) = d;
     const int v0 = d.x, v1 = d.y, ea = d.z, eb = d.w;
     // pass 0 sums the bytes announced on the barrier, pass 1 issues the copies
@@ -539,8 +539,13 @@ __device__ __forceinline__ void run_items(const SweepParams &p, const T *yin, Fi
     }
     __syncthreads();
     const Src<T, GS> src{yin, reinterpret_cast<const T *>(dyn_smem), p.stage};
-    if (threadIdx.x == 0 && (int)blockIdx.x < nitems)
-        issue_item<T, A>(p, L, blockIdx.x, buf0, &bars[0], yin);
+    // thread 0 keeps the descriptor of the item after next in a register, so
+    // no descriptor load sits on an item's path
+    int4 dnext = make_int4(0, 0, 0, 0);
+    if (threadIdx.x == 0 && (int)blockIdx.x < nitems) {
+        issue_item<T, A>(p, L, __ldg(p.desc + blockIdx.x), buf0, &bars[0], yin);
+        if ((int)(blockIdx.x + gridDim.x) < nitems) dnext = __ldg(p.desc + blockIdx.x + gridDim.x);
+    }
     int k = 0;
     bool timed_out = false;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++k) {
@@ -548,7 +553,8 @@ __device__ __forceinline__ void run_items(const SweepParams &p, const T *yin, Fi
         const int next = item + gridDim.x;
         if (threadIdx.x == 0 && next < nitems) {
             fence_async_smem();  // generic reads of that buffer precede the copy
-            issue_item<T, A>(p, L, next, b ? buf0 : buf1, &bars[b ^ 1], yin);
+            issue_item<T, A>(p, L, dnext, b ? buf0 : buf1, &bars[b ^ 1], yin);
+            if (next + (int)gridDim.x < nitems) dnext = __ldg(p.desc + next + gridDim.x);
         }
         bool ok = mbar_wait(&bars[b], (k >> 1) & 1, limit);
         if (p.test_stall && k == 0) ok = ok && mbar_wait(&bars[2], 0, limit);
