@@ -86,20 +86,23 @@ typedef struct {
  * the library defaults).  The sweep works in a degree-ordered numbering
  * (in-degree descending), where the in-degree bins are contiguous. */
 typedef struct {
-    int32_t t_lo;      /* in-degree <= t_lo: thread per vertex (default 16) */
-    int32_t t_hub;     /* in-degree >  t_hub: block per vertex, split into
-                          segments of hub_seg in-edges (default 1024,
-                          at most 4096) */
-    int32_t hub_seg;   /* in-edges per hub segment (default 2048) */
-    int32_t tile;      /* work units (in-edges + vertices) per tile of
-                          non-hub vertices, staged in shared memory
-                          (default 1024, 256 to 4096) */
+    int32_t t_lo;      /* in-degree <= t_lo: low-degree tiles, one lane per
+                          vertex (default 16, at most 32) */
+    int32_t t_hub;     /* in-degree >  t_hub: hub, split into segments of
+                          hub_seg in-edges, a warp per segment (default
+                          1024); in between: 4 to 32 lanes per vertex */
+    int32_t hub_seg;   /* in-edges per hub segment (default 2048, 256 to
+                          8192) */
+    int32_t tile;      /* work units (in-edges + vertices) per low-degree
+                          tile, whose in-edges a warp gathers into shared
+                          memory (default 256, 32 to 512) */
     int32_t deterministic_gs; /* 1: fused sweep in strict input id order on
                                  one warp (reproduces Eq. 9; n <= 65536) */
     int32_t stage_kb;  /* shared memory (KB) per block for a copy of the
                           stored vector's first entries, the most-gathered
-                          contributions in the degree-ordered ids (default
-                          0 = off; at most 160) */
+                          contributions in the degree-ordered ids (0: all
+                          the room the tiles leave, the default; -1: none;
+                          > 0: at most that many KB) */
     int32_t wait_limit;/* polls of a copy barrier before a device-side wait
                           gives up with PR_ERR_TIMEOUT (0: 4M) */
     int32_t test_stall;/* testing only: 1 makes each block's first wait

@@ -99,30 +99,34 @@ struct SolveState {
 };
 
 // Work decomposition of a sweep in the degree-ordered ids (in-degree
-// descending, so the in-degree bins are contiguous ranges):
-//   hubs  [0, nhub)        in-degree > t_hub: segments of hub_seg in-edges,
-//                          one block each
-//   tiles [nhub, n)        consecutive vertices with at most tile_c units of
-//                          work (in-edges + vertices); in a tile, in-degree
-//                          > t_lo (mid) is reduced by a warp per vertex,
-//                          the rest by a thread per vertex
+// descending, so the in-degree classes are contiguous ranges):
+//   hubs  [0, nhub)               in-degree > t_hub: segments of hub_seg
+//                                 in-edges, one warp each
+//   mid   [nhub, nhub + nmid)     t_lo < in-degree <= t_hub: four sub-ranges
+//                                 [mb[k], mb[k+1]) of 32 >> k lanes per vertex
+//                                 (in-degree > 128, > 64, > 32, the rest)
+//   low   [nhub + nmid, n)        in-degree <= t_lo: tiles of consecutive
+//                                 vertices with at most tile_c units of work
+//                                 (in-edges + vertices), one warp each
 struct Items {
     int32_t t_lo = -1, t_hub = -1, hub_seg = 0, tile_c = 0;
     int32_t nhub = 0, nmid = 0, nlow = 0;
-    int32_t nhubseg = 0;          // items of the hub role
-    int32_t ntiles = 0;           // items of the tile role
-    int32_t maxe = 0;             // largest in-edge count of a tile
+    int32_t nhubseg = 0;          // hub segments
+    int32_t mb[5] = {0, 0, 0, 0, 0};  // mid sub-range bounds
+    int32_t mi[5] = {0, 0, 0, 0, 0};  // mid items before each sub-range
+    int32_t nlt = 0;              // low tiles
+    int32_t lcap = 0;             // largest in-edge count of a low tile (+ slack)
     int32_t stage_kb = 0;         // shared-memory copy of the hottest sources
+                                  // (0: all room left, -1: none)
     int32_t wait_limit = 0;       // copy-barrier polls before a timeout (0: default)
     int32_t test_stall = 0;       // testing only: force the timeout path
     Buf hubseg_start;             // [nhub + 1] first segment of each hub
     Buf seg_acc;                  // [nhubseg] double partial sums
     Buf hub_cnt;                  // [nhub] segments finished this sweep
-    Buf tile_start;               // [ntiles + 1] first vertex of each tile
-    Buf desc;                     // [nhubseg + ntiles] int4 {v0, v1, ea, eb}:
-                                  // vertices [v0, v1), in-list slots [ea, eb)
-    int32_t idxcap = 0;           // shared-memory slots for one item's in-edges
-    int32_t vcap = 0;             // shared-memory slots for one item's vertices
+    Buf desc;                     // [nhubseg + nlt] int4: hub segments
+                                  // {hub, 0, ea, eb}, then low tiles
+                                  // {v0, v1, ea, eb}: vertices [v0, v1),
+                                  // in-list slots [ea, eb)
 };
 
 }  // namespace fpr
@@ -131,6 +135,7 @@ struct Items {
 struct pr_graph {
     int device = 0;
     int num_sms = 0;
+    int max_smem = 0;  // opt-in dynamic shared memory per block (bytes)
     int32_t n = 0;
     int64_t m = 0;
     int32_t n_dangling = 0;

@@ -81,7 +81,7 @@ __device__ __forceinline__ double next_scale(const SolveState *sx, int fp16, dou
 }
 
 template <typename Te, bool W>
-__global__ void __launch_bounds__(SWEEP_BS, 4) k_dc_resid(DCParams q)
+__global__ void __launch_bounds__(SWEEP_BS, 1) k_dc_resid(DCParams q)
 {
     SolveState *sx = q.sx, *se = q.se;
     if (sx->done) {
@@ -189,13 +189,14 @@ static int default_max_outer(pr_precision pr)
 }
 
 struct DCLaunch {
-    const void *f_r, *f_s, *f_u;
-    unsigned grid_r, grid_s, grid_u;
-    size_t smem_r, smem_s;
+    const void *f_r, *f_u;
+    unsigned grid_r, grid_u;
+    size_t smem_r;
+    SweepPlan inner;
 };
 
-static pr_status dc_graph(pr_graph *g, int key, DCParams &q, SweepParams &inner,
-                          const DCLaunch &L, cudaGraphExec_t *exec_out)
+static pr_status dc_graph(pr_graph *g, int key, DCParams &q, DCLaunch &L,
+                          cudaGraphExec_t *exec_out)
 {
     for (auto &c : g->graphs)
         if (c.key == key) {
@@ -225,8 +226,6 @@ static pr_status dc_graph(pr_graph *g, int key, DCParams &q, SweepParams &inner,
     q.h_inner = h_inner;
     q.h_outer = h_outer;
     q.use_cond = 1;
-    inner.cond = h_inner;
-    inner.use_cond = 1;
 
     // body: residual -> WHILE(inner) { correction sweep } -> update
     cudaKernelNodeParams kp = {};
@@ -248,18 +247,15 @@ static pr_status dc_graph(pr_graph *g, int key, DCParams &q, SweepParams &inner,
     cudaGraphNode_t n_inner;
     e = cudaGraphAddNode(&n_inner, body, &n_r, nullptr, 1, &ci);
     if (e != cudaSuccess) return fail(e, "inner while");
-    cudaGraph_t ibody = ci.conditional.phGraph_out[0];
-    void *args_s[] = {&inner};
-    kp.func = const_cast<void *>(L.f_s);
-    kp.gridDim = dim3(L.grid_s);
-    kp.sharedMemBytes = (unsigned)L.smem_s;
-    kp.kernelParams = args_s;
-    cudaGraphNode_t n_s;
-    e = cudaGraphAddKernelNode(&n_s, ibody, nullptr, 0, &kp);
-    if (e != cudaSuccess) return fail(e, "sweep node");
+    pr_status st = add_plan_nodes(ci.conditional.phGraph_out[0], L.inner, h_inner);
+    if (st != PR_OK) {
+        cudaGraphDestroy(top);
+        return st;
+    }
 
     kp.func = const_cast<void *>(L.f_u);
     kp.gridDim = dim3(L.grid_u);
+    kp.blockDim = dim3(256);
     kp.sharedMemBytes = 0;
     kp.kernelParams = args_q;
     cudaGraphNode_t n_u;
@@ -293,13 +289,13 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     SolveState *se = sx + 1;
     DCParams q;
     memset(&q, 0, sizeof(q));
-    fill_params(g, q.p, true, sizeof(double));
+    fill_params(g, q.p, true, sizeof(double), false);
     q.p.y0 = g->xbuf.p;
     q.p.y1 = g->xbuf.p;
     q.p.st = sx;
     q.r32 = g->rbuf.as<float>();
     SweepParams inner;
-    fill_params(g, inner, false, sizeof(Te));  // correction buffers in ybuf, FP32 1/outdeg
+    fill_params(g, inner, false, sizeof(Te), gs);  // correction buffers in ybuf, FP32 1/outdeg
     q.e0 = inner.y0;
     q.e1 = inner.y1;
     q.inv32 = g->r_inv32.as<float>();
@@ -339,27 +335,23 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     DCLaunch L;
     L.f_r = weighted ? reinterpret_cast<const void *>(&k_dc_resid<Te, true>)
                      : reinterpret_cast<const void *>(&k_dc_resid<Te, false>);
-    L.f_s = pick_sweep<Te, float>(gs, weighted);
     L.f_u = reinterpret_cast<const void *>(&k_dc_update<Te>);
-    L.smem_r = sweep_smem<double, double>(q.p, false);
-    L.smem_s = sweep_smem<Te, float>(inner, gs);
-    L.grid_r = sweep_grid(g, q.p, L.f_r, L.smem_r);
-    L.grid_s = sweep_grid(g, inner, L.f_s, L.smem_s);
-    if (L.grid_r == 0 || L.grid_s == 0) return PR_ERR_INVALID_ARG;
+    L.smem_r = layout_of<double, double, false>(q.p).total;
+    L.grid_r = sweep_grid(g, q.p.nhubseg + q.p.mi[4] + q.p.nlt, L.f_r, L.smem_r);
+    if (L.grid_r == 0) return PR_ERR_INVALID_ARG;
+    PR_TRY((make_plan<Te, float>(g, inner, gs, L.inner)));
     L.grid_u = (unsigned)ib;
     bool graph_loop = false;
     if (o->use_graph) {
         const int key = 16 | (gs ? 2 : 0) | (weighted ? 8 : 0) | (g->items.test_stall ? 32 : 0) |
-                        ((int)o->precision << 8) | (g->items.stage_kb << 16);
+                        ((int)o->precision << 8);
         cudaGraphExec_t exec;
-        PR_TRY(dc_graph(g, key, q, inner, L, &exec));
+        PR_TRY(dc_graph(g, key, q, L, &exec));
         PR_CUDA(cudaGraphLaunch(exec, s));
         graph_loop = true;
     } else {
         q.use_cond = 0;
-        inner.use_cond = 0;
         void *aq[] = {&q};
-        void *as[] = {&inner};
         for (int outer = 0; outer < 1000; ++outer) {
             PR_CUDA(cudaLaunchKernel(L.f_r, dim3(L.grid_r), dim3(SWEEP_BS), aq, L.smem_r, s));
             note_launch();
@@ -367,10 +359,7 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
             PR_CUDA(cudaStreamSynchronize(s));
             if (hs[0].done) break;
             while (true) {
-                for (int k = 0; k < 8; ++k) {
-                    PR_CUDA(cudaLaunchKernel(L.f_s, dim3(L.grid_s), dim3(SWEEP_BS), as, L.smem_s, s));
-                    note_launch();
-                }
+                for (int k = 0; k < 8; ++k) PR_TRY(launch_plan(L.inner, s));
                 PR_CUDA(cudaMemcpyAsync(hs, sx, 2 * sizeof(SolveState), cudaMemcpyDeviceToHost, s));
                 PR_CUDA(cudaStreamSynchronize(s));
                 if (hs[1].done) break;
@@ -385,7 +374,9 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     PR_LAUNCH_CHECK();
     PR_CUDA(cudaMemcpyAsync(hs, sx, 2 * sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
-    if (graph_loop) note_launch((uint64_t)hs[0].iter + hs[0].outer_iter);
+    if (graph_loop)  // residual and update kernels per outer step, the inner sweeps
+        note_launch((uint64_t)2 * hs[0].outer_iter +
+                    (uint64_t)L.inner.nlaunch * (hs[0].iter - hs[0].outer_iter));
     pr_status st = (pr_status)hs[0].status;
     if (res) {
         res->outer_iters = hs[0].outer_iter;

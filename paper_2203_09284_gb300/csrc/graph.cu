@@ -8,7 +8,7 @@
 //   3. 1/outdeg, dangling count, largest in-degree          (k_vertex_init)
 //   4. degree-ordered ids: stable radix sort of vertices by in-degree,
 //      largest first; in-lists re-sorted in the new ids
-//   5. work items: hub segments over [0, nhub), tiles over [nhub, n)
+//   5. work items: hub segments over [0, nhub), mid sub-ranges, low tiles
 //   6. (on demand) out-lists; (weighted graphs) row sums and P per slot
 #include <string.h>
 
@@ -85,17 +85,20 @@ __global__ void k_make_rcsc_keys(int64_t m, const int32_t *__restrict__ src,
 }
 
 // -------------------------------------------------------------- work items
+// counts[0]: in-degree > t_hub; counts[1]: t_lo < in-degree <= t_hub;
+// counts[2..4]: of those, in-degree > max(t_lo, 128 / 64 / 32).
 __global__ void k_count_classes(int32_t n, const int32_t *__restrict__ col_ptr, int t_lo,
                                 int t_hub, int32_t *counts)
 {
     int u = blockIdx.x * blockDim.x + threadIdx.x;
-    int deg = u < n ? col_ptr[u + 1] - col_ptr[u] : 0;
-    unsigned hub = __ballot_sync(FULL, u < n && deg > t_hub);
-    unsigned mid = __ballot_sync(FULL, u < n && deg > t_lo && deg <= t_hub);
-    if ((threadIdx.x & 31) == 0) {
-        if (hub) atomicAdd(&counts[0], __popc(hub));
-        if (mid) atomicAdd(&counts[1], __popc(mid));
-    }
+    int deg = u < n ? col_ptr[u + 1] - col_ptr[u] : -1;
+    const bool mid = deg > t_lo && deg <= t_hub;
+    unsigned b[5] = {__ballot_sync(FULL, deg > t_hub), __ballot_sync(FULL, mid),
+                     __ballot_sync(FULL, mid && deg > 128), __ballot_sync(FULL, mid && deg > 64),
+                     __ballot_sync(FULL, mid && deg > 32)};
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 5; ++k)
+            if (b[k]) atomicAdd(&counts[k], __popc(b[k]));
 }
 
 __global__ void k_hub_segments(int32_t nhub, const int32_t *__restrict__ col_ptr, int hub_seg,
@@ -105,9 +108,9 @@ __global__ void k_hub_segments(int32_t nhub, const int32_t *__restrict__ col_ptr
     if (h < nhub) nseg[h] = (col_ptr[h + 1] - col_ptr[h] + hub_seg - 1) / hub_seg;
 }
 
-// Tile k starts at the first vertex u >= nhub whose work prefix
-// (in-edges + vertices before it, counted from nhub) reaches k * c.
-__global__ void k_tile_starts(int32_t ntiles, int32_t nhub, int32_t n,
+// Tile k starts at the first vertex u >= first whose work prefix (in-edges +
+// vertices before it, counted from `first`) reaches k * c.
+__global__ void k_tile_starts(int32_t ntiles, int32_t first, int32_t n,
                               const int32_t *__restrict__ col_ptr, int32_t c, int32_t *tile_start)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -117,19 +120,19 @@ __global__ void k_tile_starts(int32_t ntiles, int32_t nhub, int32_t n,
         return;
     }
     const int64_t target = (int64_t)k * c;
-    const int32_t e0 = col_ptr[nhub];
-    int lo = nhub, hi = n;  // answer in [nhub, n]
+    const int32_t e0 = col_ptr[first];
+    int lo = first, hi = n;  // answer in [first, n]
     while (lo < hi) {
         int mid = lo + ((hi - lo) >> 1);
-        int64_t cost = (int64_t)(col_ptr[mid] - e0) + (mid - nhub);
+        int64_t cost = (int64_t)(col_ptr[mid] - e0) + (mid - first);
         if (cost >= target) hi = mid;
         else lo = mid + 1;
     }
     tile_start[k] = lo;
 }
 
-// Item descriptors {v0, v1, ea, eb}: hub segments first (one hub each), then
-// tiles.
+// Item descriptors: hub segments {hub, 0, ea, eb} first, then low tiles
+// {v0, v1, ea, eb}.
 __global__ void k_item_desc(int32_t nhubseg, int32_t nhub, const int32_t *__restrict__ hubseg_start,
                             int hub_seg, int32_t ntiles, const int32_t *__restrict__ tile_start,
                             const int32_t *__restrict__ col_ptr, int4 *desc)
@@ -145,7 +148,7 @@ __global__ void k_item_desc(int32_t nhubseg, int32_t nhub, const int32_t *__rest
         }
         const int h = lo;
         const int a = col_ptr[h] + (i - hubseg_start[h]) * hub_seg;
-        desc[i] = make_int4(h, h + 1, a, min(a + hub_seg, col_ptr[h + 1]));
+        desc[i] = make_int4(h, 0, a, min(a + hub_seg, col_ptr[h + 1]));
     } else {
         const int k = i - nhubseg;
         const int v0 = tile_start[k], v1 = tile_start[k + 1];
@@ -166,13 +169,13 @@ pr_tune effective_tune(const pr_graph *g, const pr_tune *t)
         r.wait_limit = t->wait_limit > 0 ? t->wait_limit : 0;
         r.test_stall = t->test_stall ? 1 : 0;
     }
-    r.stage_kb = r.stage_kb < 0 ? 0 : std::min(r.stage_kb, 160);
-    // a tile stages up to tile + t_hub in-edges in shared memory: both are
-    // capped at 4096 (at most 128 KB per block for the FP64 fused sweep)
-    r.t_hub = std::max(1, std::min(r.t_hub, 4096));
-    r.t_lo = std::max(0, std::min(r.t_lo, r.t_hub));
+    r.stage_kb = r.stage_kb < 0 ? -1 : std::min(r.stage_kb, 227);
+    // a low tile's in-edges (at most tile + t_lo) sit in one warp's slice of
+    // shared memory, and a lane adds up to t_lo of them
+    r.t_lo = std::max(0, std::min(r.t_lo, 32));
+    r.t_hub = std::max(r.t_lo, std::min(r.t_hub, 1 << 20));
     r.hub_seg = std::max(256, std::min(r.hub_seg, 8192));
-    r.tile = std::max(256, std::min(r.tile, 4096));
+    r.tile = std::max(32, std::min(r.tile, 512));
     return r;
 }
 
@@ -182,7 +185,30 @@ static void drop_temp(pr_graph *g, Buf &b, cudaStream_t s)
     buf_free(g, b, s);
 }
 
-// (Re)computes the bin counts, hub segments and tiles for the thresholds.
+// Scratch device memory freed when it goes out of scope (on every return
+// path); never registered with the graph.
+struct Scratch {
+    pr_graph *g;
+    cudaStream_t s;
+    Buf b;
+    Scratch(pr_graph *g_, cudaStream_t s_) : g(g_), s(s_) {}
+    ~Scratch() { buf_free(g, b, s); }
+    pr_status alloc(size_t bytes)
+    {
+        b.p = g->mem.alloc(bytes, s);
+        if (!b.p) {
+            set_error("device allocation of %zu bytes failed", bytes);
+            return PR_ERR_OOM;
+        }
+        b.bytes = bytes ? bytes : 16;
+        return PR_OK;
+    }
+    template <typename T>
+    T *as() const { return b.as<T>(); }
+};
+
+// (Re)computes the classes, hub segments, mid sub-ranges and low tiles for
+// the thresholds.
 pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
 {
     Items &it = g->items;
@@ -194,19 +220,28 @@ pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
         return PR_OK;
     const int32_t n = g->n;
     const int32_t *rcp = g->r_col_ptr.as<int32_t>();
-    Buf tmp;
-    PR_TRY(buf_alloc(g, tmp, sizeof(int32_t) * 4, s));
-    PR_CUDA(cudaMemsetAsync(tmp.p, 0, sizeof(int32_t) * 4, s));
+    Scratch tmp(g, s);
+    PR_TRY(tmp.alloc(sizeof(int32_t) * 8));
+    PR_CUDA(cudaMemsetAsync(tmp.b.p, 0, sizeof(int32_t) * 8, s));
     k_count_classes<<<(n + 255) / 256, 256, 0, s>>>(n, rcp, t.t_lo, t.t_hub, tmp.as<int32_t>());
     note_launch();
     PR_LAUNCH_CHECK();
-    int32_t h[4];
-    PR_CUDA(cudaMemcpyAsync(h, tmp.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    int32_t h[8];
+    PR_CUDA(cudaMemcpyAsync(h, tmp.b.p, sizeof(h), cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
-    drop_temp(g, tmp, s);
     it.nhub = h[0];
     it.nmid = h[1];
     it.nlow = n - h[0] - h[1];
+    // mid sub-ranges: 32, 16, 8, 4 lanes per vertex
+    const int32_t bounds[5] = {it.nhub, it.nhub + h[2], it.nhub + h[3], it.nhub + h[4],
+                               it.nhub + h[1]};
+    it.mi[0] = 0;
+    for (int k = 0; k < 4; ++k) {
+        const int per = 1 << k;  // vertices per warp
+        it.mb[k] = bounds[k];
+        it.mi[k + 1] = it.mi[k] + (bounds[k + 1] - bounds[k] + per - 1) / per;
+    }
+    it.mb[4] = bounds[4];
 
     // hub segments
     PR_TRY(buf_alloc(g, it.hubseg_start, sizeof(int32_t) * (size_t)(it.nhub + 1), s));
@@ -227,31 +262,30 @@ pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
     }
     PR_TRY(buf_alloc(g, it.seg_acc, sizeof(double) * (size_t)std::max(it.nhubseg, 1), s));
 
-    // tiles over [nhub, n)
+    // low tiles over [nhub + nmid, n)
+    const int32_t first = it.nhub + it.nmid;
     int32_t ends[2] = {0, 0};
-    PR_CUDA(cudaMemcpyAsync(&ends[0], rcp + it.nhub, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaMemcpyAsync(&ends[0], rcp + first, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaMemcpyAsync(&ends[1], rcp + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
-    const int64_t work = (int64_t)(ends[1] - ends[0]) + (n - it.nhub);
-    it.ntiles = (int32_t)((work + t.tile - 1) / t.tile);
-    PR_TRY(buf_alloc(g, it.tile_start, sizeof(int32_t) * (size_t)(it.ntiles + 1), s));
-    k_tile_starts<<<(it.ntiles + 256) / 256, 256, 0, s>>>(it.ntiles, it.nhub, n, rcp, t.tile,
-                                                          it.tile_start.as<int32_t>());
+    const int64_t work = (int64_t)(ends[1] - ends[0]) + (n - first);
+    it.nlt = (int32_t)((work + t.tile - 1) / t.tile);
+    Scratch tile_start(g, s);
+    PR_TRY(tile_start.alloc(sizeof(int32_t) * (size_t)(it.nlt + 1)));
+    k_tile_starts<<<(it.nlt + 256) / 256, 256, 0, s>>>(it.nlt, first, n, rcp, t.tile,
+                                                       tile_start.as<int32_t>());
     note_launch();
-    const int nitems = it.nhubseg + it.ntiles;
+    const int nitems = it.nhubseg + it.nlt;
     PR_TRY(buf_alloc(g, it.desc, sizeof(int4) * (size_t)std::max(nitems, 1), s));
     if (nitems > 0) {
         k_item_desc<<<(nitems + 255) / 256, 256, 0, s>>>(
-            it.nhubseg, it.nhub, it.hubseg_start.as<int32_t>(), t.hub_seg, it.ntiles,
-            it.tile_start.as<int32_t>(), rcp, it.desc.as<int4>());
+            it.nhubseg, it.nhub, it.hubseg_start.as<int32_t>(), t.hub_seg, it.nlt,
+            tile_start.as<int32_t>(), rcp, it.desc.as<int4>());
         note_launch();
     }
     PR_LAUNCH_CHECK();
-    // a tile's in-edges: fewer than tile + (in-degree of its last vertex);
-    // shared-memory capacities leave room for 16-byte widening of each range
-    it.maxe = (t.tile + t.t_hub + 3) & ~3;
-    it.idxcap = (std::max(it.maxe, t.hub_seg) + 8 + 3) & ~3;
-    it.vcap = (t.tile + 16 + 7) & ~7;
+    // a low tile holds fewer than tile + t_lo + 1 in-edges
+    it.lcap = (t.tile + t.t_lo + 8) & ~7;
     it.t_lo = t.t_lo;
     it.t_hub = t.t_hub;
     it.hub_seg = t.hub_seg;
@@ -551,7 +585,7 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
     g->tune.t_lo = 16;
     g->tune.t_hub = 1024;
     g->tune.hub_seg = 2048;
-    g->tune.tile = 1024;
+    g->tune.tile = 256;
     g->tune.deterministic_gs = 0;
     g->tune.stage_kb = 0;
     g->tune.wait_limit = 0;
@@ -560,6 +594,9 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&g->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                   g->device);
     if (e != cudaSuccess) st = cuda_status(e, "device query", __FILE__, __LINE__);
     if (st == PR_OK) st = build_all(g, src, dst, w, flags, s);
     if (st != PR_OK) {

@@ -63,9 +63,10 @@ pr_status ensure_workspace(pr_graph *g, cudaStream_t s)
     return PR_OK;
 }
 
-// Sweep parameters over the degree-ordered in-lists; stored vectors of
-// `elem` bytes per vertex in ybuf.
-void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem)
+// static shared memory of a sweep block (partial sums) plus slack
+constexpr int SWEEP_STATIC_SMEM = 2048;
+
+void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs)
 {
     Items &it = g->items;
     memset(&p, 0, sizeof(p));
@@ -75,17 +76,27 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem)
     p.outdeg = g->r_outdeg.as<int32_t>();
     p.inv = fp64 ? g->r_inv64.p : g->r_inv32.p;
     p.ew = g->weighted ? (fp64 ? g->p64_csc.p : g->p32_csc.p) : nullptr;
-    p.desc = it.desc.as<int4>();
     p.nhub = it.nhub;
+    p.hdesc = it.desc.as<int4>();
     p.nhubseg = it.nhubseg;
-    p.ntiles = it.ntiles;
-    p.t_lo = it.t_lo;
     p.hubseg_start = it.hubseg_start.as<int32_t>();
     p.seg_acc = it.seg_acc.as<double>();
     p.hub_cnt = it.hub_cnt.as<int32_t>();
-    p.idxcap = it.idxcap;
-    p.vcap = it.vcap;
-    p.stage = (int32_t)std::min<int64_t>(g->n, (int64_t)it.stage_kb * 1024 / (int64_t)elem);
+    for (int k = 0; k < 5; ++k) {
+        p.mb[k] = it.mb[k];
+        p.mi[k] = it.mi[k];
+    }
+    p.ldesc = it.desc.as<int4>() + it.nhubseg;
+    p.nlt = it.nlt;
+    p.lcap = it.lcap;
+    // staged copy: the room left beside the warp slices (or stage_kb KB)
+    const Layout L0 = make_layout(p.lcap, fp64 ? 8 : 4, (int)elem, gs, 0);
+    int64_t stage = ((int64_t)g->max_smem - L0.total - SWEEP_STATIC_SMEM) / (int64_t)elem;
+    if (it.stage_kb > 0) stage = std::min<int64_t>(stage, (int64_t)it.stage_kb * 1024 / elem);
+    if (it.stage_kb < 0) stage = 0;
+    p.stage = (int32_t)std::max<int64_t>(0, std::min<int64_t>(g->n, stage));
+    p.kinds = KIND_ALL;
+    p.close = 1;
     p.wait_limit = (uint32_t)it.wait_limit;
     p.test_stall = it.test_stall;
     p.y0 = g->ybuf.p;
@@ -93,30 +104,94 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem)
     p.st = g->state.as<SolveState>();
 }
 
-// Persistent grid: as many resident blocks as the kernel allows on every SM
-// (with its dynamic shared memory), capped by the number of work items.
-unsigned sweep_grid(const pr_graph *g, const SweepParams &p, const void *func, size_t smem)
+// One persistent block of SWEEP_BS threads per SM (fewer if there are fewer
+// items than warps); 0 with the error set if the shared memory does not fit.
+unsigned sweep_grid(const pr_graph *g, int nitems, const void *func, size_t smem)
 {
-    const int nitems = p.nhubseg + p.ntiles;
-    int max_smem = 0;
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, g->device);
-    if (smem > (size_t)max_smem) {
-        set_error("the tile and hub sizes need %zu bytes of shared memory per block (limit %d): "
-                  "use a smaller tile, t_hub, hub_seg or stage_kb",
-                  smem, max_smem);
+    if (smem + SWEEP_STATIC_SMEM > (size_t)g->max_smem) {
+        set_error("a sweep block needs %zu bytes of shared memory (limit %d): use a smaller "
+                  "tile or t_lo",
+                  smem + SWEEP_STATIC_SMEM, g->max_smem);
         return 0;
     }
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, SWEEP_BS, smem) !=
-            cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    const int grid = std::min(nitems, per_sm * g->num_sms);
+    cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int grid = std::min((nitems + SWEEP_WARPS - 1) / SWEEP_WARPS, g->num_sms);
     return (unsigned)std::max(grid, 1);
+}
+
+template <typename T, typename A>
+static const void *pick_sweep(bool gs, bool weighted)
+{
+    if (gs)
+        return weighted ? reinterpret_cast<const void *>(&k_sweep<T, A, true, true>)
+                        : reinterpret_cast<const void *>(&k_sweep<T, A, true, false>);
+    return weighted ? reinterpret_cast<const void *>(&k_sweep<T, A, false, true>)
+                    : reinterpret_cast<const void *>(&k_sweep<T, A, false, false>);
+}
+
+template <typename T, typename A>
+pr_status make_plan(pr_graph *g, const SweepParams &p, bool gs, SweepPlan &plan)
+{
+    plan.func = pick_sweep<T, A>(gs, p.ew != nullptr);
+    plan.smem = gs ? layout_of<T, A, true>(p).total : layout_of<T, A, false>(p).total;
+    const int nmid_items = p.mi[4];
+    if (gs && p.nhubseg > 0) {
+        plan.nlaunch = 2;
+        plan.p[0] = p;
+        plan.p[0].kinds = KIND_HUB;
+        plan.p[0].close = 0;
+        plan.p[1] = p;
+        plan.p[1].kinds = KIND_MID | KIND_LOW;
+        plan.p[1].close = 1;
+        plan.grid[0] = sweep_grid(g, p.nhubseg, plan.func, plan.smem);
+        plan.grid[1] = sweep_grid(g, nmid_items + p.nlt, plan.func, plan.smem);
+    } else {
+        plan.nlaunch = 1;
+        plan.p[0] = p;
+        plan.p[0].kinds = KIND_ALL;
+        plan.p[0].close = 1;
+        plan.grid[0] = sweep_grid(g, p.nhubseg + nmid_items + p.nlt, plan.func, plan.smem);
+        plan.grid[1] = 1;
+    }
+    if (plan.grid[0] == 0 || plan.grid[1] == 0) return PR_ERR_INVALID_ARG;
+    return PR_OK;
+}
+template pr_status make_plan<double, double>(pr_graph *, const SweepParams &, bool, SweepPlan &);
+template pr_status make_plan<float, float>(pr_graph *, const SweepParams &, bool, SweepPlan &);
+template pr_status make_plan<__nv_bfloat16, float>(pr_graph *, const SweepParams &, bool,
+                                                   SweepPlan &);
+template pr_status make_plan<__half, float>(pr_graph *, const SweepParams &, bool, SweepPlan &);
+
+pr_status add_plan_nodes(cudaGraph_t body, SweepPlan &plan, cudaGraphConditionalHandle h)
+{
+    cudaGraphNode_t prev = nullptr;
+    for (int k = 0; k < plan.nlaunch; ++k) {
+        plan.p[k].cond = h;
+        plan.p[k].use_cond = 1;
+        void *args[] = {&plan.p[k]};
+        cudaKernelNodeParams kp = {};
+        kp.func = const_cast<void *>(plan.func);
+        kp.gridDim = dim3(plan.grid[k]);
+        kp.blockDim = dim3(plan.block);
+        kp.sharedMemBytes = (unsigned)plan.smem;
+        kp.kernelParams = args;
+        cudaGraphNode_t node;
+        PR_CUDA(cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+        prev = node;
+    }
+    return PR_OK;
+}
+
+pr_status launch_plan(SweepPlan &plan, cudaStream_t s)
+{
+    for (int k = 0; k < plan.nlaunch; ++k) {
+        plan.p[k].use_cond = 0;
+        void *args[] = {&plan.p[k]};
+        PR_CUDA(cudaLaunchKernel(plan.func, dim3(plan.grid[k]), dim3(plan.block), args,
+                                 plan.smem, s));
+        note_launch();
+    }
+    return PR_OK;
 }
 
 void release_graphs(pr_graph *g)
@@ -128,9 +203,7 @@ void release_graphs(pr_graph *g)
     g->graphs.clear();
 }
 
-// Instantiates (or reuses) a graph: WHILE(cond) { kernel<<<grid, block, smem>>>(p) }.
-pr_status loop_graph(pr_graph *g, int key, const void *func, unsigned grid, unsigned block,
-                     size_t smem, SweepParams &p, cudaGraphExec_t *exec_out)
+pr_status loop_graph(pr_graph *g, int key, SweepPlan &plan, cudaGraphExec_t *exec_out)
 {
     for (auto &c : g->graphs)
         if (c.key == key) {
@@ -156,20 +229,13 @@ pr_status loop_graph(pr_graph *g, int key, const void *func, unsigned grid, unsi
         cudaGraphDestroy(graph);
         return cuda_status(e, "cudaGraphAddNode(while)", __FILE__, __LINE__);
     }
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    p.cond = h;
-    p.use_cond = 1;
-    void *args[] = {&p};
-    cudaKernelNodeParams kp = {};
-    kp.func = const_cast<void *>(func);
-    kp.gridDim = dim3(grid);
-    kp.blockDim = dim3(block);
-    kp.sharedMemBytes = (unsigned)smem;
-    kp.kernelParams = args;
-    cudaGraphNode_t knode;
-    e = cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp);
+    pr_status st = add_plan_nodes(cp.conditional.phGraph_out[0], plan, h);
+    if (st != PR_OK) {
+        cudaGraphDestroy(graph);
+        return st;
+    }
     cudaGraphExec_t exec = nullptr;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    e = cudaGraphInstantiate(&exec, graph, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(graph);
         return cuda_status(e, "loop graph", __FILE__, __LINE__);
@@ -214,31 +280,6 @@ pr_status finish_result(pr_graph *g, pr_result *res, cudaStream_t s, int outer)
     return st;
 }
 
-template <typename T, typename A>
-const void *pick_sweep(bool gs, bool weighted)
-{
-    if (gs)
-        return weighted ? reinterpret_cast<const void *>(&k_sweep<T, A, true, true>)
-                        : reinterpret_cast<const void *>(&k_sweep<T, A, true, false>);
-    return weighted ? reinterpret_cast<const void *>(&k_sweep<T, A, false, true>)
-                    : reinterpret_cast<const void *>(&k_sweep<T, A, false, false>);
-}
-template const void *pick_sweep<double, double>(bool, bool);
-template const void *pick_sweep<float, float>(bool, bool);
-template const void *pick_sweep<__nv_bfloat16, float>(bool, bool);
-template const void *pick_sweep<__half, float>(bool, bool);
-
-// Dynamic shared memory of a sweep launch with these parameters.
-template <typename T, typename A>
-size_t sweep_smem(const SweepParams &p, bool gs)
-{
-    return gs ? layout_of<T, A, true>(p).total : layout_of<T, A, false>(p).total;
-}
-template size_t sweep_smem<double, double>(const SweepParams &, bool);
-template size_t sweep_smem<float, float>(const SweepParams &, bool);
-template size_t sweep_smem<__nv_bfloat16, float>(const SweepParams &, bool);
-template size_t sweep_smem<__half, float>(const SweepParams &, bool);
-
 // Runs the sweep loop for precision T (plain forms).
 template <typename T, typename A>
 static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn, double *x_out,
@@ -253,7 +294,7 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
         return PR_ERR_UNSUPPORTED;
     }
     SweepParams p;
-    fill_params(g, p, fp64, sizeof(T));
+    fill_params(g, p, fp64, sizeof(T), gs);
     const int32_t *n2o = g->n2o.as<int32_t>();
     const int32_t *o2n = g->o2n.as<int32_t>();
     if (serial) {  // strict Eq. 9 order on the input ids
@@ -264,6 +305,16 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
         n2o = o2n = nullptr;
     }
     p.renorm = gs ? 1 : 0;
+    SweepPlan plan;
+    if (serial) {
+        plan.func = reinterpret_cast<const void *>(&k_sweep_serial<T, A>);
+        plan.nlaunch = 1;
+        plan.p[0] = p;
+        plan.grid[0] = 1;
+        plan.block = 32;
+    } else {
+        PR_TRY((make_plan<T, A>(g, p, gs, plan)));
+    }
     SolveState *hs = g->host_state;
     init_state(g, o, *hs);
     PR_CUDA(cudaMemcpyAsync(g->state.p, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
@@ -273,38 +324,19 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
     note_launch();
     PR_LAUNCH_CHECK();
 
-    const void *func;
-    unsigned grid, block;
-    size_t smem = 0;
-    if (serial) {
-        func = reinterpret_cast<const void *>(&k_sweep_serial<T, A>);
-        grid = 1;
-        block = 32;
-    } else {
-        func = pick_sweep<T, A>(gs, weighted);
-        smem = sweep_smem<T, A>(p, gs);
-        grid = sweep_grid(g, p, func, smem);
-        if (grid == 0) return PR_ERR_INVALID_ARG;
-        block = SWEEP_BS;
-    }
     bool graph_loop = false;
     if (o->use_graph) {
         const int key = (fp64 ? 1 : 0) | (gs ? 2 : 0) | (serial ? 4 : 0) | (weighted ? 8 : 0) |
-                        (g->items.test_stall ? 32 : 0) | (g->items.stage_kb << 16);
+                        (g->items.test_stall ? 32 : 0);
         cudaGraphExec_t exec;
-        PR_TRY(loop_graph(g, key, func, grid, block, smem, p, &exec));
+        PR_TRY(loop_graph(g, key, plan, &exec));
         PR_CUDA(cudaGraphLaunch(exec, s));
         graph_loop = true;
     } else {
-        p.use_cond = 0;
-        void *args[] = {&p};
         int launched = 0;
         while (launched < o->max_iter) {
             const int batch = std::min(16, o->max_iter - launched);
-            for (int k = 0; k < batch; ++k) {
-                PR_CUDA(cudaLaunchKernel(func, dim3(grid), dim3(block), args, smem, s));
-                note_launch();
-            }
+            for (int k = 0; k < batch; ++k) PR_TRY(launch_plan(plan, s));
             launched += batch;
             PR_CUDA(cudaMemcpyAsync(g->host_state, g->state.p, sizeof(SolveState),
                                     cudaMemcpyDeviceToHost, s));
@@ -318,7 +350,8 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
     note_launch();
     PR_LAUNCH_CHECK();
     pr_status st = finish_result(g, res, s, 0);
-    if (graph_loop) note_launch((uint64_t)g->host_state->iter + 1);  // loop sweeps + final check
+    // loop sweeps + the launch that sees the stop flag
+    if (graph_loop) note_launch((uint64_t)plan.nlaunch * (g->host_state->iter + 1));
     return st;
 }
 

@@ -12,17 +12,37 @@ pr_status check_device(pr_graph *g);
 pr_status ensure_workspace(pr_graph *g, cudaStream_t s);
 // validation, work items for the options' thresholds, workspace
 pr_status prepare_solve(pr_graph *g, const pr_options *o, pr_tune &tn, cudaStream_t s);
-void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem);
-unsigned sweep_grid(const pr_graph *g, const SweepParams &p, const void *func, size_t smem);
-pr_status loop_graph(pr_graph *g, int key, const void *func, unsigned grid, unsigned block,
-                     size_t smem, SweepParams &p, cudaGraphExec_t *exec_out);
+// Sweep parameters over the degree-ordered in-lists; stored vectors of
+// `elem` bytes per vertex in ybuf; the staged copy takes the shared memory
+// left beside the warp slices of this arithmetic (fp64) and variant (gs).
+void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs);
+
+// Grid of a persistent sweep kernel over `nitems` warp items with `smem`
+// bytes of dynamic shared memory (0 with the error set if it does not fit).
+unsigned sweep_grid(const pr_graph *g, int nitems, const void *func, size_t smem);
+
+// The launches of one sweep: one launch over all items, or for the fused
+// sweep the hub segments first and then the rest (so the second launch's
+// staged copy holds the new hub values).
+struct SweepPlan {
+    const void *func = nullptr;
+    size_t smem = 0;
+    int nlaunch = 0;
+    unsigned block = SWEEP_BS;
+    unsigned grid[2] = {0, 0};
+    SweepParams p[2];
+};
+template <typename T, typename A>
+pr_status make_plan(pr_graph *g, const SweepParams &p, bool gs, SweepPlan &plan);
+// adds the plan's launches as a chain of kernel nodes of `body`
+pr_status add_plan_nodes(cudaGraph_t body, SweepPlan &plan, cudaGraphConditionalHandle h);
+// launches one sweep of the plan (no graph)
+pr_status launch_plan(SweepPlan &plan, cudaStream_t s);
+// Instantiates (or reuses) a graph: WHILE(cond) { the plan's launches }.
+pr_status loop_graph(pr_graph *g, int key, SweepPlan &plan, cudaGraphExec_t *exec_out);
 void init_state(pr_graph *g, const pr_options *o, SolveState &h);
 pr_status finish_result(pr_graph *g, pr_result *res, cudaStream_t s, int outer);
 pr_status solve_dc(pr_graph *g, const pr_options *o, const pr_tune &tn, double *x_out,
                    pr_result *res, cudaStream_t s);
-template <typename T, typename A>
-const void *pick_sweep(bool gs, bool weighted);
-template <typename T, typename A>
-size_t sweep_smem(const SweepParams &p, bool gs);
 
 }  // namespace fpr

@@ -1,46 +1,54 @@
-// sweep.cuh -- the fused PageRank sweep (one kernel per sweep).
+// sweep.cuh -- the fused PageRank sweep.
 //
-// One launch gathers the stored contribution vector through the in-lists,
+// One sweep gathers the stored contribution vector through the in-lists,
 // applies teleport and dangling mass, writes the new stored value, and
 // accumulates the sweep's L1/max error, dangling mass and total; the block
 // that finishes last turns those sums into the next sweep's scalars and the
 // stop decision (Algorithm 1/2 `while error > threshold`).
 //
-// Everything runs in the degree-ordered numbering (in-degree descending):
-// hubs are the ids [0, nhub).  Stored vector y (one entry per vertex):
+// Everything runs in the degree-ordered numbering (in-degree descending), so
+// the in-degree classes are contiguous ranges of ids:
+//   hubs  [0, nhub)               in-degree > t_hub
+//   mid   [nhub, nhub + nmid)     t_lo < in-degree <= t_hub
+//   low   [nhub + nmid, n)        in-degree <= t_lo
+// and the most-gathered contributions (in R-MAT-like graphs, the sources of
+// about half of all edges) sit in the first few tens of thousands of ids.
+//
+// Stored vector y (one entry per vertex):
 //   y_u = x~_u * inv_outdeg[u]   if u has out-edges (its contribution, the
 //                                 paper's contributionList entry)
 //   y_u = x~_u                    if u is dangling (never gathered), or for
 //                                 weighted graphs (P is applied per in-edge)
-// where the true rank is x_u = sigma * x~_u.  Reading a vertex's own old rank
-// and gathering its in-neighbours touch the same array.
+// where the true rank is x_u = sigma * x~_u.
 //
-// Work items, in launch order (heavy first), each described by
-// {v0, v1, ea, eb} (vertices [v0, v1), in-list slots [ea, eb)):
-//   hub segment  hub_seg in-edges of one hub (v1 = v0 + 1) summed by a block;
-//                the block finishing a hub's last segment adds the segment
-//                sums in order and updates the hub (block per vertex)
-//   tile         consecutive non-hub vertices with at most `tile` units of
-//                work, reduced by a warp per vertex (in-degree > t_lo) or a
-//                thread per vertex (in-degree <= t_lo)
-// A persistent grid takes the items round-robin.  Each block double-buffers
-// them in shared memory: while it works on one item, bulk copies (TMA,
-// cp.async.bulk) bring the next item's contiguous streams -- in-list indices,
-// offsets, out-degrees, 1/outdeg, old stored values, right-hand side, edge
-// weights -- so the only memory latency left on the item's path is the random
-// gather of the in-neighbours' contributions, all of which are in flight at
-// once.  The per-vertex epilogue is a functor, so the same traversal serves
-// the PageRank sweep, the correction sweep and the FP64 residual sweep of the
+// Launch shape: one persistent block of 1024 threads per SM.  The block first
+// copies y[0, stage) into shared memory with one bulk (TMA) copy completed on
+// an mbarrier, so every warp of the SM reads the hottest contributions from
+// shared memory; all other gathers go to L2/HBM.  Then each warp works on its
+// own items with no block-wide synchronisation (items taken round-robin by
+// warp, a fixed order, so the sweep's sums are reproducible):
+//   hub segment  hub_seg in-edges of one hub, summed by a warp (16-byte index
+//                loads, eight gathers in flight per lane); the warp finishing
+//                a hub's last segment adds the segment sums in order and
+//                updates the hub
+//   mid group    32/G consecutive mid vertices, G lanes per vertex (G = 32,
+//                16, 8 or 4 as the in-degree falls: more than 128, 64, 32,
+//                else), same streaming gather, then a G-lane reduction
+//   low tile     consecutive low-degree vertices with at most `tile` units of
+//                work: the warp gathers all their in-edges into its slice of
+//                shared memory, then one lane per vertex adds its own
+// The per-vertex epilogue is a functor, so the same traversal serves the
+// PageRank sweep, the correction sweep and the FP64 residual sweep of the
 // defect-correction forms.
 //
 // Jacobi (Algorithm 1, Eq. 2): reads y[iter & 1], writes the other buffer.
 // Fused (Algorithm 2, Eq. 9): one buffer updated in place with L2-coherent
 // loads and stores, so a vertex sees whichever contribution is there (new if
-// its in-neighbour was already updated in this sweep).  Inside a tile, the
-// vertices are updated warp-vertices first, then thread-vertices in rounds;
-// a later vertex reads the new values of the tile's earlier vertices from
-// shared memory.  After each fused sweep the iterate is rescaled to sum 1 by
-// folding 1/sum into sigma.
+// its in-neighbour was already updated in this sweep).  The hubs are updated
+// by a first launch, so the second launch's shared-memory copy already holds
+// their new values; inside a low tile, a vertex reads the new values of the
+// tile's earlier vertices from shared memory.  After each fused sweep the
+// iterate is rescaled to sum 1 by folding 1/sum into sigma.
 #pragma once
 
 #include "common.cuh"
@@ -48,8 +56,11 @@
 
 namespace fpr {
 
-constexpr int SWEEP_BS = 256;
+constexpr int SWEEP_BS = 1024;
+constexpr int SWEEP_WARPS = SWEEP_BS / 32;
 constexpr uint32_t DEFAULT_WAIT_LIMIT = 1u << 22;
+
+enum : int32_t { KIND_HUB = 1, KIND_MID = 2, KIND_LOW = 4, KIND_ALL = 7 };
 
 struct SweepParams {
     int32_t n;
@@ -58,13 +69,21 @@ struct SweepParams {
     const int32_t *__restrict__ outdeg;
     const void *inv;              // A[n]: 1/outdeg in the arithmetic type
     const void *ew;               // A[m]: P per in-list slot (weighted) or null
-    const int4 *desc;             // [nhubseg + ntiles] item descriptors
-    int32_t nhub, nhubseg, ntiles, t_lo;
+    int32_t nhub;                 // hubs are [0, nhub)
+    const int4 *hdesc;            // [nhubseg] {hub, 0, first slot, end slot}
+    int32_t nhubseg;
     const int32_t *hubseg_start;  // [nhub + 1]
     double *seg_acc;              // [nhubseg]
     int32_t *hub_cnt;             // [nhub]
-    int32_t idxcap, vcap;         // shared-memory capacity of one item
+    int32_t mb[5];                // mid sub-range k = [mb[k], mb[k+1]): 32 >> k
+                                  // lanes per vertex
+    int32_t mi[5];                // items before sub-range k (mi[4]: all mid items)
+    const int4 *ldesc;            // [nlt] low tiles {v0, v1, first slot, end slot}
+    int32_t nlt;
+    int32_t lcap;                 // per-warp slots for a low tile's in-edges
     int32_t stage;                // y[0, stage) is copied to shared memory
+    int32_t kinds;                // items of this launch (KIND_* bits)
+    int32_t close;                // this launch closes the sweep
     uint32_t wait_limit;
     int32_t test_stall;
     void *y0, *y1;                // stored vectors
@@ -193,7 +212,7 @@ struct SweepFin {
 template <typename A>
 __device__ __forceinline__ void block_partials(SolveState *st, const Part<A> &pt)
 {
-    __shared__ double red[4][SWEEP_BS / 32];
+    __shared__ double red[4][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double l1 = warp_sum(static_cast<double>(pt.l1));
     double lm = warp_max(static_cast<double>(pt.lmax));
@@ -304,44 +323,30 @@ __device__ __forceinline__ void close_sweep(const SweepParams &p)
 // ------------------------------------------------------- shared memory
 __host__ __device__ constexpr uint32_t a16(size_t b) { return (uint32_t)((b + 15) & ~(size_t)15); }
 
-// Layout of the dynamic shared memory of a sweep block:
-//   [staged y[0, stage)] [item buffer 0] [item buffer 1] [gathered terms]
-//   [fused sweep: slot sources, new tile values] [barriers]
-// and of one item buffer:
-//   [descriptor int4] [indices] [offsets] [out-degrees] [1/outdeg]
-//   [old stored values] [right-hand side] [edge weights]
+// Dynamic shared memory of a sweep block:
+//   [staged y[0, stage)] [barriers] [32 warp slices]
+// and of one warp slice: [gathered terms, lcap] and for the fused sweep
+// [in-tile source of each slot (int16, -1 if none), lcap].
 struct Layout {
-    uint32_t idx, cp, od, inv, yo, rhs, ew, buf;          // within a buffer
-    uint32_t buf0, buf1, vals, sidx, fresh, bars, total;  // within the block
+    uint32_t bars, warps, wvals, wsidx, wbytes, total;
 };
 
-__host__ __device__ inline Layout make_layout(int idxcap, int vcap, int sa, int st, bool rhs,
-                                              bool w, bool gs, int stage)
+__host__ __device__ inline Layout make_layout(int lcap, int sa, int st, bool gs, int stage)
 {
     Layout L;
-    L.idx = 16;
-    L.cp = L.idx + a16((size_t)idxcap * 4);
-    L.od = L.cp + a16((size_t)vcap * 4);
-    L.inv = L.od + a16((size_t)vcap * 4);
-    L.yo = L.inv + a16((size_t)vcap * sa);
-    L.rhs = L.yo + a16((size_t)vcap * st);
-    L.ew = L.rhs + (rhs ? a16((size_t)vcap * sa) : 0);
-    L.buf = L.ew + (w ? a16((size_t)idxcap * sa) : 0);
-    L.buf0 = a16((size_t)stage * st);
-    L.buf1 = L.buf0 + L.buf;
-    L.vals = L.buf1 + L.buf;
-    L.sidx = L.vals + a16((size_t)idxcap * sa);
-    L.fresh = L.sidx + (gs ? a16((size_t)idxcap * 4) : 0);
-    L.bars = L.fresh + (gs ? a16((size_t)vcap * st) : 0);
-    L.total = L.bars + 32;  // three 8-byte barriers
+    L.bars = a16((size_t)stage * st);
+    L.warps = L.bars + 32;
+    L.wvals = 0;
+    L.wsidx = a16((size_t)lcap * sa);
+    L.wbytes = L.wsidx + (gs ? a16((size_t)lcap * 2) : 0);
+    L.total = L.warps + SWEEP_WARPS * L.wbytes;
     return L;
 }
 
 template <typename T, typename A, bool GS>
 __host__ __device__ inline Layout layout_of(const SweepParams &p)
 {
-    return make_layout(p.idxcap, p.vcap, sizeof(A), sizeof(T), p.rhs != nullptr, p.ew != nullptr,
-                       GS, p.stage);
+    return make_layout(p.lcap, sizeof(A), sizeof(T), GS, p.stage);
 }
 
 // Where a gathered contribution comes from: the copy of y[0, nstaged) in
@@ -357,226 +362,254 @@ struct Src {
     }
 };
 
-// Thread 0: bulk copies of the item with descriptor d into `buf`, completing
-// on `bar`.  Ranges are widened to 16-byte boundaries (the arrays are padded
-// for it).
-template <typename T, typename A>
-__device__ __forceinline__ void issue_item(const SweepParams &p, const Layout &L, int4 d,
-                                           unsigned char *buf, uint64_t *bar, const T *yin)
+// This lane's share of the sum over in-list slots [a, e) when G lanes (gl =
+// lane index among them) stream one list: 16-byte index loads, two of them
+// (eight gathers) in flight per lane.
+template <int G, typename T, typename A, bool GS, bool W>
+__device__ __forceinline__ A group_stream(const SweepParams &p, const Src<T, GS> &src, int a,
+                                          int e, int gl)
 {
-    *reinterpret_cast<int4 *>(buf) = d;
-    const int v0 = d.x, v1 = d.y, ea = d.z, eb = d.w;
-    // pass 0 sums the bytes announced on the barrier, pass 1 issues the copies
-    uint32_t tx = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1) mbar_expect_tx(bar, tx);
-        auto range = [&](uint32_t off, const void *base, int elem, int lo, int hi) {
-            const int al = 16 / elem;
-            const int s = lo & ~(al - 1), e = (hi + al - 1) & ~(al - 1);
-            if (e <= s) return;
-            const uint32_t bytes = (uint32_t)(e - s) * (uint32_t)elem;
-            if (pass == 0) tx += bytes;
-            else bulk_load(buf + off, static_cast<const char *>(base) + (size_t)s * elem, bytes, bar);
-        };
-        range(L.idx, p.row_idx, 4, ea, eb);
-        range(L.cp, p.col_ptr, 4, v0, v1 + 1);
-        range(L.od, p.outdeg, 4, v0, v1);
-        range(L.inv, p.inv, sizeof(A), v0, v1);
-        range(L.yo, yin, sizeof(T), v0, v1);
-        if (p.rhs) range(L.rhs, p.rhs, sizeof(A), v0, v1);
-        if (p.ew) range(L.ew, p.ew, sizeof(A), ea, eb);
+    A acc = 0;
+    const A *ew = static_cast<const A *>(p.ew);
+    for (int j0 = (a & ~3) + 4 * gl; j0 < e; j0 += 8 * G) {
+        const int j1 = j0 + 4 * G;
+        const int4 q0 = __ldg(reinterpret_cast<const int4 *>(p.row_idx + j0));
+        const int4 q1 = j1 < e ? __ldg(reinterpret_cast<const int4 *>(p.row_idx + j1))
+                               : make_int4(0, 0, 0, 0);
+        const int v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        A got[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int s = (c < 4 ? j0 : j1) + (c & 3);
+            got[c] = (s >= a && s < e) ? to_a<A>(src(v[c])) : A(0);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int s = (c < 4 ? j0 : j1) + (c & 3);
+            if constexpr (W) got[c] = (s >= a && s < e) ? ew[s] * got[c] : A(0);
+            acc += got[c];
+        }
+    }
+    return acc;
+}
+
+template <int G, typename A>
+__device__ __forceinline__ A group_sum(A v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+template <typename A>
+__device__ __forceinline__ A rhs_of(const SweepParams &p, int u, A base)
+{
+    return p.rhs ? static_cast<const A *>(p.rhs)[u] : base;
+}
+
+// hub segment i (one warp)
+template <typename T, typename A, bool GS, bool W, typename Fin>
+__device__ __forceinline__ void hub_item(const SweepParams &p, int i, const Src<T, GS> &src,
+                                         Fin &fin, int lane)
+{
+    const int4 d = __ldg(p.hdesc + i);
+    const int h = d.x;
+    A acc = group_stream<32, T, A, GS, W>(p, src, d.z, d.w, lane);
+    const double s = warp_sum(static_cast<double>(acc));
+    if (lane == 0) {
+        p.seg_acc[i] = s;
+        __threadfence();
+        const int s0 = p.hubseg_start[h];
+        const int nseg = p.hubseg_start[h + 1] - s0;
+        if (atomicAdd(&p.hub_cnt[h], 1) == nseg - 1) {
+            __threadfence();
+            const volatile double *sa = p.seg_acc;
+            double all = 0;
+            for (int j = 0; j < nseg; ++j) all += sa[s0 + j];
+            p.hub_cnt[h] = 0;
+            fin(h, static_cast<A>(all), p.outdeg[h], static_cast<const A *>(p.inv)[h],
+                ld_y<T, GS>(src.y, h), rhs_of<A>(p, h, fin.base()));
+        }
     }
 }
 
-// Works on one item whose streams are in `buf`.
-template <typename T, typename A, bool GS, bool W, typename Fin>
-__device__ __forceinline__ void do_item(const SweepParams &p, const Layout &L, int item,
-                                        const unsigned char *buf, unsigned char *smem,
-                                        const Src<T, GS> &src, Fin &fin)
+// mid vertices [v0, min(v0 + 32 / G, v_end)): G lanes per vertex
+template <int G, typename T, typename A, bool GS, bool W, typename Fin>
+__device__ __forceinline__ void mid_group(const SweepParams &p, int v0, int v_end,
+                                          const Src<T, GS> &src, Fin &fin, int lane)
 {
-    __shared__ double hub_red[SWEEP_BS / 32];
-    const int4 d = *reinterpret_cast<const int4 *>(buf);
+    const int gl = lane & (G - 1);
+    const int u = v0 + lane / G;
+    const bool act = u < v_end;
+    int a = 0, e = 0, od = 0;
+    A inv = 0, r = 0;
+    T yo{};
+    if (act) {
+        a = __ldg(p.col_ptr + u);
+        e = __ldg(p.col_ptr + u + 1);
+        if (gl == 0) {  // the epilogue's inputs, issued before the gathers
+            od = __ldg(p.outdeg + u);
+            inv = static_cast<const A *>(p.inv)[u];
+            yo = ld_y<T, GS>(src.y, u);
+            r = rhs_of<A>(p, u, fin.base());
+        }
+    }
+    A acc = group_stream<G, T, A, GS, W>(p, src, a, e, gl);
+    acc = group_sum<G>(acc);
+    if (act && gl == 0) fin(u, acc, od, inv, yo, r);
+}
+
+// low tile k (one warp): in-edges gathered into the warp's shared slice,
+// then one lane per vertex
+template <typename T, typename A, bool GS, bool W, typename Fin>
+__device__ __forceinline__ void low_item(const SweepParams &p, int k, const Src<T, GS> &src,
+                                         Fin &fin, int lane, unsigned char *slice,
+                                         const Layout &L)
+{
+    const int4 d = __ldg(p.ldesc + k);
     const int v0 = d.x, v1 = d.y, ea = d.z, eb = d.w;
-    const int ne = eb - ea;
-    constexpr int alA = 16 / sizeof(A), alT = 16 / sizeof(T);
-    const int *idx = reinterpret_cast<const int *>(buf + L.idx) - (ea & ~3);
-    const int *cp = reinterpret_cast<const int *>(buf + L.cp) - (v0 & ~3);
-    const int *od = reinterpret_cast<const int *>(buf + L.od) - (v0 & ~3);
-    const A *inv = reinterpret_cast<const A *>(buf + L.inv) - (v0 & ~(alA - 1));
-    const T *yo = reinterpret_cast<const T *>(buf + L.yo) - (v0 & ~(alT - 1));
-    const A *rhs = reinterpret_cast<const A *>(buf + L.rhs) - (v0 & ~(alA - 1));
-    const A *ew = reinterpret_cast<const A *>(buf + L.ew) - (ea & ~(alA - 1));
-    A *vals = reinterpret_cast<A *>(smem + L.vals);
-    int *sidx = reinterpret_cast<int *>(smem + L.sidx);
-    T *fresh = reinterpret_cast<T *>(smem + L.fresh);
-    const bool has_rhs = p.rhs != nullptr;
-
-    // phase A: every in-edge, four independent gathers per thread per step
-    for (int s0 = threadIdx.x; s0 < ne; s0 += 4 * SWEEP_BS) {
-        int v[4];
-        A got[4];
+    A *vals = reinterpret_cast<A *>(slice + L.wvals);
+    short *sidx = reinterpret_cast<short *>(slice + L.wsidx);
+    const A *ew = static_cast<const A *>(p.ew);
+    // inputs of this lane's first vertex, issued before the gathers
+    int u = v0 + lane;
+    int a0 = 0, e0 = 0, od0 = 0;
+    A inv0 = 0, r0 = 0;
+    T yo0{};
+    if (u < v1) {
+        a0 = __ldg(p.col_ptr + u);
+        e0 = __ldg(p.col_ptr + u + 1);
+        od0 = __ldg(p.outdeg + u);
+        inv0 = static_cast<const A *>(p.inv)[u];
+        yo0 = ld_y<T, GS>(src.y, u);
+        r0 = rhs_of<A>(p, u, fin.base());
+    }
+    // gathers: eight slots per lane in flight
+    for (int j0 = (ea & ~3) + 4 * lane; j0 < eb; j0 += 256) {
+        const int j1 = j0 + 128;
+        const int4 q0 = __ldg(reinterpret_cast<const int4 *>(p.row_idx + j0));
+        const int4 q1 = j1 < eb ? __ldg(reinterpret_cast<const int4 *>(p.row_idx + j1))
+                                : make_int4(0, 0, 0, 0);
+        const int v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+        A got[8];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int s = s0 + c * SWEEP_BS;
-            v[c] = s < ne ? idx[ea + s] : 0;
+        for (int c = 0; c < 8; ++c) {
+            const int s = (c < 4 ? j0 : j1) + (c & 3);
+            got[c] = (s >= ea && s < eb) ? to_a<A>(src(v[c])) : A(0);
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int s = s0 + c * SWEEP_BS;
-            got[c] = s < ne ? to_a<A>(src(v[c])) : A(0);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int s = s0 + c * SWEEP_BS;
-            if (s < ne) {
-                vals[s] = W ? ew[ea + s] * got[c] : got[c];
-                if constexpr (GS) sidx[s] = v[c];
+        for (int c = 0; c < 8; ++c) {
+            const int s = (c < 4 ? j0 : j1) + (c & 3);
+            if (s >= ea && s < eb) {
+                vals[s - ea] = W ? ew[s] * got[c] : got[c];
+                if constexpr (GS)
+                    sidx[s - ea] = (v[c] >= v0 && v[c] < v1) ? (short)(v[c] - v0) : (short)-1;
             }
         }
     }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = SWEEP_BS / 32;
-
-    if (v0 < p.nhub) {
-        // hub segment: block sum, then the hub's last segment finishes it
-        double s = 0;
-        for (int i = threadIdx.x; i < ne; i += SWEEP_BS) s += static_cast<double>(vals[i]);
-        s = warp_sum(s);
-        if (lane == 0) hub_red[warp] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double tot = 0;
-            for (int w = 0; w < nw; ++w) tot += hub_red[w];
-            const int h = v0;
-            p.seg_acc[item] = tot;
-            __threadfence();
-            const int s0 = p.hubseg_start[h];
-            const int nseg = p.hubseg_start[h + 1] - s0;
-            if (atomicAdd(&p.hub_cnt[h], 1) == nseg - 1) {
-                __threadfence();
-                const volatile double *sa = p.seg_acc;
-                double all = 0;
-                for (int j = 0; j < nseg; ++j) all += sa[s0 + j];
-                p.hub_cnt[h] = 0;
-                fin(h, static_cast<A>(all), od[h], inv[h], yo[h], has_rhs ? rhs[h] : fin.base());
-            }
-        }
-        return;
-    }
-
-    // tile: first vertex with in-degree <= t_lo (degrees are non-increasing)
-    int vm;
-    {
-        int lo = v0, hi = v1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (cp[mid + 1] - cp[mid] <= p.t_lo) hi = mid;
-            else lo = mid + 1;
-        }
-        vm = lo;
-    }
-    // phase B1: in-degree > t_lo: warp per vertex
-    for (int u = v0 + warp; u < vm; u += nw) {
-        const int a = cp[u] - ea, e = cp[u + 1] - ea;
-        A acc = 0;
-        for (int i = a + lane; i < e; i += 32) acc += vals[i];
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            const T yn = fin(u, acc, od[u], inv[u], yo[u], has_rhs ? rhs[u] : fin.base());
-            if constexpr (GS) fresh[u - v0] = yn;
-        }
-    }
-    if constexpr (GS) __syncthreads();
-    // phase B2: thread per vertex, in rounds of the block size
-    for (int u0 = vm; u0 < v1; u0 += SWEEP_BS) {
-        const int u = u0 + threadIdx.x;
+    __syncwarp();
+    T *yself = static_cast<T *>(const_cast<T *>(src.y));
+    for (int u0 = v0; u0 < v1; u0 += 32) {
+        u = u0 + lane;
         if (u < v1) {
-            const int a = cp[u] - ea, e = cp[u + 1] - ea;
+            int a, e, od;
+            A inv, r;
+            T yo;
+            if (u0 == v0) {
+                a = a0, e = e0, od = od0, inv = inv0, r = r0, yo = yo0;
+            } else {
+                a = __ldg(p.col_ptr + u);
+                e = __ldg(p.col_ptr + u + 1);
+                od = __ldg(p.outdeg + u);
+                inv = static_cast<const A *>(p.inv)[u];
+                yo = ld_y<T, GS>(src.y, u);
+                r = rhs_of<A>(p, u, fin.base());
+            }
             A acc = 0;
-            for (int i = a; i < e; ++i) {
+            for (int i = a - ea; i < e - ea; ++i) {
                 A val = vals[i];
                 if constexpr (GS) {
-                    // in-tile source already updated in this sweep: new value
-                    const int v = sidx[i];
-                    if (v >= v0 && v < u0) {
-                        const A nv = to_a<A>(fresh[v - v0]);
+                    // a source of this tile updated in an earlier round of
+                    // this sweep: its new value (written before the last
+                    // __syncwarp, so visible to this lane)
+                    const int t = sidx[i];
+                    if (t >= 0 && v0 + t < u0) {
+                        const A nv = to_a<A>(ld_y<T, true>(yself, v0 + t));
                         val = W ? ew[ea + i] * nv : nv;
                     }
                 }
                 acc += val;
             }
-            const T yn = fin(u, acc, od[u], inv[u], yo[u], has_rhs ? rhs[u] : fin.base());
-            if constexpr (GS) fresh[u - v0] = yn;
+            fin(u, acc, od, inv, yo, r);
         }
-        if constexpr (GS) __syncthreads();
+        __syncwarp();
     }
 }
 
-// Persistent, double-buffered loop over the items of this block (items
-// blockIdx, blockIdx + G, ... in that fixed order, so every block's partial
-// sums are reproducible).  Returns false if a copy wait gave up.
+// mid item j (a group of vertices of one sub-range)
+template <typename T, typename A, bool GS, bool W, typename Fin>
+__device__ __forceinline__ void mid_item(const SweepParams &p, int j, const Src<T, GS> &src,
+                                         Fin &fin, int lane)
+{
+    if (j < p.mi[1]) mid_group<32, T, A, GS, W>(p, p.mb[0] + j, p.mb[1], src, fin, lane);
+    else if (j < p.mi[2]) mid_group<16, T, A, GS, W>(p, p.mb[1] + 2 * (j - p.mi[1]), p.mb[2], src, fin, lane);
+    else if (j < p.mi[3]) mid_group<8, T, A, GS, W>(p, p.mb[2] + 4 * (j - p.mi[2]), p.mb[3], src, fin, lane);
+    else mid_group<4, T, A, GS, W>(p, p.mb[3] + 8 * (j - p.mi[3]), p.mb[4], src, fin, lane);
+}
+
+// The persistent sweep body: staging, then this warp's items of the kinds of
+// this launch (hub segments, then mid groups, then low tiles), taken
+// round-robin by global warp index.  If a bounded wait gives up, the error
+// is recorded in the state and the block skips its items.
 template <typename T, typename A, bool GS, bool W, typename Fin>
 __device__ __forceinline__ void run_items(const SweepParams &p, const T *yin, Fin &fin)
 {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     const Layout L = layout_of<T, A, GS>(p);
     uint64_t *bars = reinterpret_cast<uint64_t *>(dyn_smem + L.bars);
-    unsigned char *const buf0 = dyn_smem + L.buf0, *const buf1 = dyn_smem + L.buf1;
-    const int nitems = p.nhubseg + p.ntiles;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t limit = p.wait_limit ? p.wait_limit : DEFAULT_WAIT_LIMIT;
+    // staged copy of the hottest contributions: one bulk copy (a snapshot,
+    // for the fused sweep)
+    const uint32_t sbytes = a16((size_t)p.stage * sizeof(T));
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init(&bars[2], 1);  // nothing ever arrives here (timeout test)
+        mbar_init(&bars[1], 1);  // nothing ever arrives here (timeout test)
         mbar_init_fence();
     }
-    // staged copy of the hottest contributions (snapshot for the fused sweep)
-    if (p.stage > 0) {
-        const int4 *s = reinterpret_cast<const int4 *>(yin);
-        int4 *dst = reinterpret_cast<int4 *>(dyn_smem);
-        const int nvec = (int)(a16((size_t)p.stage * sizeof(T)) / 16);
-        for (int i = threadIdx.x; i < nvec; i += SWEEP_BS) dst[i] = GS ? __ldcg(s + i) : __ldg(s + i);
-    }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bars[0], sbytes);
+        if (sbytes) bulk_load(dyn_smem, yin, sbytes, &bars[0]);
+    }
+    bool ok = mbar_wait(&bars[0], 0, limit);
+    if (p.test_stall) ok = ok && mbar_wait(&bars[1], 0, limit);
+    if (__syncthreads_or(!ok)) {
+        mbar_wait(&bars[0], 0, limit);  // drain the copy before leaving
+        if (threadIdx.x == 0) atomicCAS(&p.st->error, 0, (int)PR_ERR_TIMEOUT);
+        return;
+    }
     const Src<T, GS> src{yin, reinterpret_cast<const T *>(dyn_smem), p.stage};
-    // thread 0 keeps the descriptor of the item after next in a register, so
-    // no descriptor load sits on an item's path
-    int4 dnext = make_int4(0, 0, 0, 0);
-    if (threadIdx.x == 0 && (int)blockIdx.x < nitems) {
-        issue_item<T, A>(p, L, __ldg(p.desc + blockIdx.x), buf0, &bars[0], yin);
-        if ((int)(blockIdx.x + gridDim.x) < nitems) dnext = __ldg(p.desc + blockIdx.x + gridDim.x);
+    unsigned char *slice = dyn_smem + L.warps + warp * L.wbytes;
+    const int gw = blockIdx.x * SWEEP_WARPS + warp;
+    const int nw = gridDim.x * SWEEP_WARPS;
+    const int nh = (p.kinds & KIND_HUB) ? p.nhubseg : 0;
+    const int nm = (p.kinds & KIND_MID) ? p.mi[4] : 0;
+    const int nl = (p.kinds & KIND_LOW) ? p.nlt : 0;
+    for (int i = gw; i < nh + nm + nl; i += nw) {
+        if (i < nh) hub_item<T, A, GS, W>(p, i, src, fin, lane);
+        else if (i < nh + nm) mid_item<T, A, GS, W>(p, i - nh, src, fin, lane);
+        else low_item<T, A, GS, W>(p, i - nh - nm, src, fin, lane, slice, L);
     }
-    int k = 0;
-    bool timed_out = false;
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x, ++k) {
-        const int b = k & 1;
-        const int next = item + gridDim.x;
-        if (threadIdx.x == 0 && next < nitems) {
-            fence_async_smem();  // generic reads of that buffer precede the copy
-            issue_item<T, A>(p, L, dnext, b ? buf0 : buf1, &bars[b ^ 1], yin);
-            if (next + (int)gridDim.x < nitems) dnext = __ldg(p.desc + next + gridDim.x);
-        }
-        bool ok = mbar_wait(&bars[b], (k >> 1) & 1, limit);
-        if (p.test_stall && k == 0) ok = ok && mbar_wait(&bars[2], 0, limit);
-        if (__syncthreads_or(!ok)) {
-            // drain this block's copies still in flight, then report
-            mbar_wait(&bars[b], (k >> 1) & 1, limit);
-            if (next < nitems) mbar_wait(&bars[b ^ 1], ((k + 1) >> 1) & 1, limit);
-            timed_out = true;
-            break;
-        }
-        do_item<T, A, GS, W>(p, L, item, b ? buf1 : buf0, dyn_smem, src, fin);
-        __syncthreads();  // the buffer and the gathered terms are reused
-    }
-    if (timed_out && threadIdx.x == 0) atomicCAS(&p.st->error, 0, (int)PR_ERR_TIMEOUT);
 }
 
 template <typename T, typename A, bool GS, bool W>
-__global__ void __launch_bounds__(SWEEP_BS, 4) k_sweep(SweepParams p)
+__global__ void __launch_bounds__(SWEEP_BS, 1) k_sweep(SweepParams p)
 {
     SolveState *st = p.st;
     if (st->done) {
-        if (p.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(p.cond, 0u);
+        if (p.close && p.use_cond && blockIdx.x == 0 && threadIdx.x == 0)
+            cudaGraphSetConditional(p.cond, 0u);
         return;
     }
     const int iter = st->iter;
@@ -592,7 +625,7 @@ __global__ void __launch_bounds__(SWEEP_BS, 4) k_sweep(SweepParams p)
     SweepFin<T, A, GS, W> fin(p, load_ctx<A>(st), yout);
     run_items<T, A, GS, W>(p, yin, fin);
     block_partials<A>(st, fin.pt);
-    if (last_block(st) && threadIdx.x == 0) close_sweep(p);
+    if (p.close && last_block(st) && threadIdx.x == 0) close_sweep(p);
 }
 
 // Fused sweep in strict increasing input-id order (Eq. 9 exactly): one warp,
@@ -609,15 +642,13 @@ __global__ void k_sweep_serial(SweepParams p)
     T *y = static_cast<T *>(p.y0);
     SweepFin<T, A, true, false> fin(p, load_ctx<A>(st), y);
     const A *inv = static_cast<const A *>(p.inv);
-    const A *rhs = static_cast<const A *>(p.rhs);
     const int lane = threadIdx.x & 31;
     for (int u = 0; u < p.n; ++u) {
         const int a = p.col_ptr[u], e = p.col_ptr[u + 1];
         A acc = 0;
         for (int i = a + lane; i < e; i += 32) acc += to_a<A>(ld_y<T, true>(y, p.row_idx[i]));
         acc = warp_sum(acc);
-        if (lane == 0)
-            fin(u, acc, p.outdeg[u], inv[u], ld_y<T, true>(y, u), rhs ? rhs[u] : fin.base());
+        if (lane == 0) fin(u, acc, p.outdeg[u], inv[u], ld_y<T, true>(y, u), rhs_of<A>(p, u, fin.base()));
         __syncwarp();
     }
     block_partials<A>(st, fin.pt);

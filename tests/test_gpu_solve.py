@@ -154,7 +154,8 @@ def test_closed_forms_on_gpu(gs):
                                   {"t_lo": 1, "t_hub": 1, "hub_seg": 512, "tile": 300,
                                    "stage_kb": -1},
                                   {"t_lo": 64, "t_hub": 4096, "hub_seg": 1024, "tile": 1024,
-                                   "stage_kb": 8}])
+                                   "stage_kb": 8},
+                                  {"t_lo": 8, "t_hub": 1 << 20, "tile": 64}])
 def test_bin_thresholds_do_not_change_the_result(s16, tune):
     n, src, dst, og, g, star = s16
     x, r = g.solve(threshold=0.0, max_iter=6, tune=tune)
