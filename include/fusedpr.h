@@ -52,7 +52,8 @@ typedef enum {
     PR_ERR_CUDA = 3,        /* CUDA runtime error; see pr_last_error() */
     PR_NOT_CONVERGED = 4,   /* max_iter reached; outputs hold the last iterate */
     PR_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
-    PR_ERR_UNSUPPORTED = 6  /* option combination not implemented */
+    PR_ERR_UNSUPPORTED = 6, /* option combination not implemented */
+    PR_ERR_NUMERIC = 7      /* a non-finite value appeared in the iterate */
 } pr_status;
 
 typedef enum { PR_JACOBI = 0, PR_FUSED_GS = 1 } pr_variant;
@@ -60,8 +61,9 @@ typedef enum { PR_JACOBI = 0, PR_FUSED_GS = 1 } pr_variant;
 /* Arithmetic of the sweep.  *_DC forms run the cheap sweep on a correction
  * and recompute the residual in FP64 between inner solves (defect
  * correction); the stop value is then the FP64 residual
- * || (1-d)/n + d M x - x ||_1.  BF16/FP16 store the gathered vector scaled by
- * a power of two (n for the rank itself) with FP32 accumulation. */
+ * || (1-d)/n + d M x - x ||_1.  The correction is stored in FP32, BF16 or
+ * FP16 (FP16 scaled by a power of two that keeps every entry below 2^14)
+ * with FP32 accumulation. */
 typedef enum {
     PR_FP64 = 0,
     PR_FP32 = 1,
@@ -100,9 +102,9 @@ typedef struct {
                                  one warp (reproduces Eq. 9; n <= 65536) */
     int32_t stage_kb;  /* shared memory (KB) per block for a copy of the
                           stored vector's first entries, the most-gathered
-                          contributions in the degree-ordered ids (0: all
-                          the room the tiles leave, the default; -1: none;
-                          > 0: at most that many KB) */
+                          contributions in the degree-ordered ids (0:
+                          the default, 32; -1: none; > 0: that many KB, at
+                          most the room the tiles leave) */
     int32_t wait_limit;/* polls of a copy barrier before a device-side wait
                           gives up with PR_ERR_TIMEOUT (0: 4M) */
     int32_t test_stall;/* testing only: 1 makes each block's first wait
@@ -201,15 +203,21 @@ pr_status pr_solve(pr_graph *g, const pr_options *o, double *x_out, pr_result *r
 /*
  * Personalised PageRank for B teleport vectors at once (multi right-hand
  * side sweep): column b teleports to the single vertex seeds[b] and its
- * dangling mass is redistributed to the same vertex.  FP32 sweep
- * (o->precision must be PR_FP32); each column stops on its own L1 error.
+ * dangling mass is redistributed to the same vertex.  Jacobi sweep in FP32
+ * or FP64 (o->precision PR_FP32 or PR_FP64, o->variant PR_JACOBI, L1 norm);
+ * each column stops on its own L1 change and keeps that iterate.  An FP32
+ * column whose change stops decreasing above the threshold (its rounding
+ * floor) stops too, with status PR_NOT_CONVERGED.  Start vector 1/n.
  *   seeds  device int32 [B], ids in [0, n)
- *   X_out  device float [n][B] (vertex-major, column b at stride B),
- *          each column normalised to sum 1
- *   res    host [B], nullable
+ *   X_out  device [n][B] (vertex-major, column b at stride B) of float for
+ *          PR_FP32 or double for PR_FP64, each column normalised to sum 1
+ *   res    host [B], nullable: per-column sweeps, last change, status
+ * Returns PR_OK if every column converged, else PR_NOT_CONVERGED (outputs
+ * still written) or an error.  Columns run in passes of 256 (FP32) or 128
+ * (FP64); the handle keeps two n x pass-width iterates.
  */
 pr_status pr_solve_batched(pr_graph *g, const pr_options *o, int32_t B, const int32_t *seeds,
-                           float *X_out, pr_result *res, void *stream);
+                           void *X_out, pr_result *res, void *stream);
 
 /*
  * Solves G independent graphs in one sequence of launches (each sweep is one

@@ -19,7 +19,7 @@ from . import _build
 
 __all__ = [
     "PR_OK", "PR_ERR_INVALID_ARG", "PR_ERR_OOM", "PR_ERR_CUDA", "PR_NOT_CONVERGED",
-    "PR_ERR_TIMEOUT", "PR_ERR_UNSUPPORTED", "PR_JACOBI", "PR_FUSED_GS", "PR_FP64", "PR_FP32",
+    "PR_ERR_TIMEOUT", "PR_ERR_UNSUPPORTED", "PR_ERR_NUMERIC", "PR_JACOBI", "PR_FUSED_GS", "PR_FP64", "PR_FP32",
     "PR_FP32_DC", "PR_BF16_DC", "PR_FP16_DC", "PR_NORM_L1", "PR_NORM_LINF", "PR_BUILD_CSR",
     "PrOptions", "PrResult", "PrTune", "PrAllocator", "PageRankError", "lib", "library_path",
     "pr_options_default", "pr_graph_create", "pr_graph_destroy", "pr_graph_info",
@@ -28,7 +28,7 @@ __all__ = [
 ]
 
 PR_OK, PR_ERR_INVALID_ARG, PR_ERR_OOM, PR_ERR_CUDA = 0, 1, 2, 3
-PR_NOT_CONVERGED, PR_ERR_TIMEOUT, PR_ERR_UNSUPPORTED = 4, 5, 6
+PR_NOT_CONVERGED, PR_ERR_TIMEOUT, PR_ERR_UNSUPPORTED, PR_ERR_NUMERIC = 4, 5, 6, 7
 PR_JACOBI, PR_FUSED_GS = 0, 1
 PR_FP64, PR_FP32, PR_FP32_DC, PR_BF16_DC, PR_FP16_DC = 0, 1, 2, 3, 4
 PR_NORM_L1, PR_NORM_LINF = 0, 1
@@ -345,8 +345,8 @@ class Graph:
     def solve_batched(self, seeds, out=None, stream=None, **kw):
         kw.setdefault("precision", "fp32")
         B = int(seeds.numel())
-        X = out if out is not None else torch.empty((self.n, B), dtype=torch.float32,
-                                                    device="cuda")
+        dt = torch.float64 if kw["precision"] == "fp64" else torch.float32
+        X = out if out is not None else torch.empty((self.n, B), dtype=dt, device="cuda")
         res = pr_solve_batched(self.handle, make_options(**kw), seeds, X, stream)
         return X, res
 
@@ -355,3 +355,45 @@ class Graph:
         gd = torch.empty(1, dtype=torch.float64, device="cuda") if want_d else None
         res = pr_backward(self.handle, make_options(**kw), x, grad_x, gw, gd, stream)
         return gw, gd, res
+
+
+def solve_multi(graphs, outs=None, stream=None, **kw):
+    """Solves several graphs together (pr_solve_multi); returns the result
+    vectors (float64, input ids) and one PrResult per graph."""
+    xs = outs if outs is not None else [torch.empty(g.n, dtype=torch.float64, device="cuda")
+                                        for g in graphs]
+    res = pr_solve_multi([g.handle for g in graphs], make_options(**kw), xs, stream)
+    return xs, res
+
+
+class PageRankFn(torch.autograd.Function):
+    """x = PageRank of the graph (src -> dst, n vertices) with raw edge weights
+    w (row-normalised inside) and damping d, differentiable in w and d.
+
+    ``PageRankFn.apply(w, d, src, dst, n, opts)``: w float tensor [m] on the
+    GPU, d a 0-dim tensor, src/dst int32 device tensors, opts a dict of solve
+    options (threshold, max_iter, precision of the forward, ``adjoint`` =
+    options of the reverse solve).  Backward returns (dL/dw, dL/dd, None, ...)
+    from pr_backward's adjoint solve at the forward's fixed point."""
+
+    @staticmethod
+    def forward(ctx, w, d, src, dst, n, opts=None):
+        opts = dict(opts or {})
+        adj = dict(opts.pop("adjoint", {}))
+        g = Graph(n, src, dst, w=w.detach().to(torch.float32).contiguous())
+        x, _ = g.solve(d=float(d), **opts)
+        ctx.graph, ctx.d, ctx.adj = g, float(d), adj
+        ctx.w_dtype, ctx.d_dtype = w.dtype, d.dtype
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        (x,) = ctx.saved_tensors
+        g = ctx.graph
+        adj = dict(ctx.adj)
+        adj.setdefault("threshold", 1e-13)
+        gw, gd, _ = g.backward(x, grad_x.to(torch.float64).contiguous(), d=ctx.d, **adj)
+        g.close()
+        ctx.graph = None
+        return (gw.to(ctx.w_dtype), gd.reshape(()).to(ctx.d_dtype), None, None, None, None)

@@ -94,7 +94,11 @@ struct SolveState {
     double rnorm;     // defect correction: ||r||_1 of the current outer step
     double inner_tol; // defect correction: inner stop threshold (true units)
     double inner_rel;
-    double mass_target; // fused defect correction: exact sum of the correction
+    double mass_target; // defect correction: exact sum of the correction,
+                        // sum(r) / (1-d), in true units
+    double shift;       // fused defect correction: e += shift * Y64 pending
+                        // (stored units), set by the sweep's last block
+    unsigned int shift_ticket;  // blocks of the shift kernel done
     double *history;
 };
 
@@ -117,7 +121,7 @@ struct Items {
     int32_t nlt = 0;              // low tiles
     int32_t lcap = 0;             // largest in-edge count of a low tile (+ slack)
     int32_t stage_kb = 0;         // shared-memory copy of the hottest sources
-                                  // (0: all room left, -1: none)
+                                  // (KB; <= 0: none)
     int32_t wait_limit = 0;       // copy-barrier polls before a timeout (0: default)
     int32_t test_stall = 0;       // testing only: force the timeout path
     Buf hubseg_start;             // [nhub + 1] first segment of each hub
@@ -163,7 +167,21 @@ struct pr_graph {
     fpr::Buf rbuf;      // n x 8 bytes: residual / right-hand side
     fpr::Buf state;     // SolveState
     fpr::Buf aux;       // scratch for batched / multi / adjoint
+
+    // batched personalised PageRank: hub segments of the row gather
+    // (vertices [0, bnhub) with more than BATCH_SEG in-edges), iterates and
+    // per-column state
+    int32_t bnhub = -1, bnseg = 0;
+    fpr::Buf bseg_start, bseg_cnt, bseg_desc;
+    fpr::Buf bx0, bx1, bpart, bcols;
     fpr::SolveState *host_state = nullptr;  // pinned mirror
+
+    // reverse mode: the graph with every edge reversed (its in-lists are
+    // this graph's out-lists), built on the first pr_backward, and
+    // P_uv = w_uv / s_u per slot of its degree-ordered in-lists
+    pr_graph *rev = nullptr;
+    fpr::Buf adj_p64, adj_p32;  // P_uv per reversed slot
+    fpr::Buf adj_s;             // s_u (sum of u's raw out-weights) per reversed id
 
     // cached CUDA graphs of the solve loop
     struct Cached {

@@ -38,16 +38,16 @@ struct DCParams {
     int weighted;
 };
 
-// Epilogue of the residual sweep: r_u in FP64, stored as FP32, and the first
-// correction iterate e = r written in the correction's stored form.
+// Epilogue of the residual sweep: r_u in FP64, stored as FP32; unless the
+// correction needs a scale (FP16), also the first correction iterate e = r
+// in the correction's stored form.  A non-finite r_u ends the solve with
+// PR_ERR_NUMERIC.
 template <typename Te>
 struct ResidFin {
     const DCParams &q;
     Ctx<double> c;
-    float rscale;  // 1 / sigma_e
     Part<double> pt;
-    __device__ ResidFin(const DCParams &q_, const Ctx<double> &c_, float rs)
-        : q(q_), c(c_), rscale(rs) {}
+    __device__ ResidFin(const DCParams &q_, const Ctx<double> &c_) : q(q_), c(c_) {}
     __device__ __forceinline__ double base() const { return c.base; }
     __device__ __forceinline__ double operator()(int u, double acc, int od, double, double yo,
                                                  double)
@@ -56,26 +56,55 @@ struct ResidFin {
         const double xold = plain ? yo : yo * static_cast<double>(od);
         const double xnew = c.base + c.d * (c.sig * (acc + c.dt));
         const double r = xnew - c.sig * xold;
+        if (!isfinite(r)) atomicCAS(&q.sx->error, 0, (int)PR_ERR_NUMERIC);
         const float rf = static_cast<float>(r);
         q.r32[u] = rf;
-        const float es = rf * rscale;
-        static_cast<Te *>(q.e0)[u] = from_a<Te>(plain ? es : es * q.inv32[u]);
+        if (!q.fp16) static_cast<Te *>(q.e0)[u] = from_a<Te>(plain ? rf : rf * q.inv32[u]);
         const double ar = fabs(r);
         pt.l1 += ar;
         pt.lmax = ar > pt.lmax ? ar : pt.lmax;
-        pt.sm += es;
-        if (od == 0) pt.dm += es;
+        pt.sm += rf;
+        if (od == 0) pt.dm += rf;
         return xnew;
     }
 };
 
-__device__ __forceinline__ double next_scale(const SolveState *sx, int fp16, double rnorm_pred,
-                                             double n)
+// Fused correction sweeps drift in the sum of e (the dangling mass is taken
+// at sweep start while values change in place), which slows them far below
+// the Jacobi rate.  The solution's sum is known, so after each sweep
+//   e <- e + beta x,   beta = (sum(r)/(1-d) - sum(e)) / sum(x)
+// restores it along the current PageRank estimate: in stored units
+// e~ += shift * Y64.  The last block clears the pending shift.
+template <typename Te>
+__global__ void k_dc_shift(DCParams q)
 {
-    if (!fp16) return 1.0;
-    // correction entries average ||r||_1 / (n (1-d)); bring them near 1
-    double target = n * (1.0 - sx->d) / fmax(rnorm_pred, 1e-300);
-    int k = (int)lrint(log2(target));
+    SolveState *se = q.se;
+    const double gam = se->shift;
+    Te *e = static_cast<Te *>(q.e0);
+    const int n = q.p.n;
+    if (gam != 0.0) {
+        const float g32 = static_cast<float>(gam);
+        for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x)
+            e[u] = from_a<Te>(to_a<float>(e[u]) + g32 * static_cast<float>(q.y64[u]));
+    }
+    __shared__ bool is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&se->shift_ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (is_last && threadIdx.x == 0) {
+        se->shift = 0.0;
+        se->shift_ticket = 0;
+    }
+}
+
+// FP16 correction scale sigma_e = 2^-k: the stored entries are bounded by
+// ||e||_1 / sigma_e <= ||r||_1 / ((1-d) sigma_e) (M does not increase the
+// 1-norm, so neither the iterates nor the solution of e = r + d M e exceed
+// it), which k keeps below 2^14, far from FP16's largest value 65504.
+__device__ __forceinline__ double fp16_scale(double rnorm, double d)
+{
+    if (!(rnorm > 0.0)) return 1.0;
+    int k = (int)floor(log2(16384.0 * (1.0 - d) / rnorm));
     k = max(-120, min(120, k));
     return ldexp(1.0, -k);
 }
@@ -88,12 +117,12 @@ __global__ void __launch_bounds__(SWEEP_BS, 1) k_dc_resid(DCParams q)
         if (q.use_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(q.h_inner, 0u);
         return;
     }
-    ResidFin<Te> fin(q, load_ctx<double>(sx), static_cast<float>(1.0 / sx->scale));
+    ResidFin<Te> fin(q, load_ctx<double>(sx));
     run_items<double, double, false, W>(q.p, q.y64, fin);
     block_partials<double>(sx, fin.pt);
     if (!(last_block(sx) && threadIdx.x == 0)) return;
-    double res, resmax, dang_e, sum_e;
-    take_sums(sx, res, resmax, dang_e, sum_e);
+    double res, resmax, dang_r, sum_r;
+    take_sums(sx, res, resmax, dang_r, sum_r);
     sx->outer_iter += 1;
     const int total = sx->iter + 1;
     sx->iter = total;
@@ -111,11 +140,16 @@ __global__ void __launch_bounds__(SWEEP_BS, 1) k_dc_resid(DCParams q)
         sx->status = error ? error : (conv ? PR_OK : PR_NOT_CONVERGED);
         se->done = 1;
     } else {
+        const double scale = q.fp16 ? fp16_scale(res, sx->d) : 1.0;
+        sx->scale = scale;
         se->iter = 0;
         se->done = 0;
-        se->dang = dang_e;
-        se->sum = sum_e;
-        se->sigma = sx->scale;
+        se->dang = dang_r / scale;
+        se->sum = sum_r / scale;
+        se->sigma = scale;
+        // 1^T (I - d M) = (1-d) 1^T: the correction sums to sum(r) / (1-d)
+        se->mass_target = sum_r / (1.0 - sx->d);
+        se->shift = 0.0;
         // inner stop on the L1 change of e (true units); the last outer step
         // need not over-solve below the outer threshold
         se->tau = fmax(sx->inner_rel * res, 0.05 * sx->tau);
@@ -157,15 +191,25 @@ __global__ void k_dc_update(DCParams q)
     sx->sum = sum;
     sx->dang = dang;
     sx->sigma = sum > 0 ? 1.0 / sum : 1.0;
-    // predicted size of the next residual: the inner solve's target
-    sx->scale = next_scale(sx, q.fp16, fmax(se->tau, sx->tau), (double)n);
     __threadfence();
     if (q.use_cond) cudaGraphSetConditional(q.h_outer, 1u);
 }
 
-__global__ void k_dc_first_scale(SolveState *sx, int fp16, double n)
+// FP16 correction: e = r / sigma_e in the stored form, once the residual
+// kernel has chosen sigma_e from ||r||_1.
+template <typename Te>
+__global__ void k_dc_first_e(DCParams q)
 {
-    sx->scale = next_scale(sx, fp16, 1.0, n);
+    const SolveState *se = q.se;
+    if (q.sx->done || se->done) return;
+    const float rs = static_cast<float>(1.0 / se->sigma);
+    Te *e = static_cast<Te *>(q.e0);
+    const int n = q.p.n;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const bool plain = q.weighted || q.p.outdeg[u] == 0;
+        const float es = q.r32[u] * rs;
+        e[u] = from_a<Te>(plain ? es : es * q.inv32[u]);
+    }
 }
 
 static double default_eta(pr_precision pr)
@@ -190,6 +234,8 @@ static int default_max_outer(pr_precision pr)
 
 struct DCLaunch {
     const void *f_r, *f_u;
+    const void *f_shift;  // fused inner sweeps only
+    const void *f_e;      // FP16 only
     unsigned grid_r, grid_u;
     size_t smem_r;
     SweepPlan inner;
@@ -238,6 +284,16 @@ static pr_status dc_graph(pr_graph *g, int key, DCParams &q, DCLaunch &L,
     cudaGraphNode_t n_r;
     e = cudaGraphAddKernelNode(&n_r, body, nullptr, 0, &kp);
     if (e != cudaSuccess) return fail(e, "residual node");
+    if (L.f_e) {  // FP16: the first correction iterate, after the scale is known
+        kp.func = const_cast<void *>(L.f_e);
+        kp.gridDim = dim3(L.grid_u);
+        kp.blockDim = dim3(256);
+        kp.sharedMemBytes = 0;
+        cudaGraphNode_t n_e;
+        e = cudaGraphAddKernelNode(&n_e, body, &n_r, 1, &kp);
+        if (e != cudaSuccess) return fail(e, "first correction node");
+        n_r = n_e;
+    }
 
     cudaGraphNodeParams ci = {};
     ci.type = cudaGraphNodeTypeConditional;
@@ -247,10 +303,21 @@ static pr_status dc_graph(pr_graph *g, int key, DCParams &q, DCLaunch &L,
     cudaGraphNode_t n_inner;
     e = cudaGraphAddNode(&n_inner, body, &n_r, nullptr, 1, &ci);
     if (e != cudaSuccess) return fail(e, "inner while");
-    pr_status st = add_plan_nodes(ci.conditional.phGraph_out[0], L.inner, h_inner);
+    cudaGraphNode_t n_last = nullptr;
+    pr_status st = add_plan_nodes(ci.conditional.phGraph_out[0], L.inner, h_inner, &n_last);
     if (st != PR_OK) {
         cudaGraphDestroy(top);
         return st;
+    }
+    if (L.f_shift) {
+        kp.func = const_cast<void *>(L.f_shift);
+        kp.gridDim = dim3(L.grid_u);
+        kp.blockDim = dim3(256);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = args_q;
+        cudaGraphNode_t n_sh;
+        e = cudaGraphAddKernelNode(&n_sh, ci.conditional.phGraph_out[0], &n_last, 1, &kp);
+        if (e != cudaSuccess) return fail(e, "shift node");
     }
 
     kp.func = const_cast<void *>(L.f_u);
@@ -311,11 +378,13 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     inner.st_outer = sx;
     inner.dc = 1;
     inner.renorm = 0;
+    inner.shift = gs ? 1 : 0;
 
     SolveState *hs = g->host_state;
     init_state(g, o, hs[0]);
     hs[0].max_outer = o->max_outer > 0 ? o->max_outer : default_max_outer(o->precision);
     hs[0].inner_rel = o->inner_rel > 0 ? o->inner_rel : default_eta(o->precision);
+    hs[0].scale = 1.0;
     memset(&hs[1], 0, sizeof(SolveState));
     hs[1].d = o->d;
     hs[1].base = hs[0].base;
@@ -328,14 +397,14 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     k_init<double, double><<<ib, 256, 0, s>>>(n, o->x0, g->n2o.as<int32_t>(), q.p.outdeg, q.inv64,
                                              q.y64, sx, 1, weighted ? 1 : 0);
     note_launch();
-    k_dc_first_scale<<<1, 1, 0, s>>>(sx, q.fp16, (double)n);
-    note_launch();
     PR_LAUNCH_CHECK();
 
     DCLaunch L;
     L.f_r = weighted ? reinterpret_cast<const void *>(&k_dc_resid<Te, true>)
                      : reinterpret_cast<const void *>(&k_dc_resid<Te, false>);
     L.f_u = reinterpret_cast<const void *>(&k_dc_update<Te>);
+    L.f_shift = gs ? reinterpret_cast<const void *>(&k_dc_shift<Te>) : nullptr;
+    L.f_e = fp16 ? reinterpret_cast<const void *>(&k_dc_first_e<Te>) : nullptr;
     L.smem_r = layout_of<double, double, false>(q.p).total;
     L.grid_r = sweep_grid(g, q.p.nhubseg + q.p.mi[4] + q.p.nlt, L.f_r, L.smem_r);
     if (L.grid_r == 0) return PR_ERR_INVALID_ARG;
@@ -355,11 +424,21 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
         for (int outer = 0; outer < 1000; ++outer) {
             PR_CUDA(cudaLaunchKernel(L.f_r, dim3(L.grid_r), dim3(SWEEP_BS), aq, L.smem_r, s));
             note_launch();
+            if (L.f_e) {
+                PR_CUDA(cudaLaunchKernel(L.f_e, dim3(L.grid_u), dim3(256), aq, 0, s));
+                note_launch();
+            }
             PR_CUDA(cudaMemcpyAsync(hs, sx, 2 * sizeof(SolveState), cudaMemcpyDeviceToHost, s));
             PR_CUDA(cudaStreamSynchronize(s));
             if (hs[0].done) break;
             while (true) {
-                for (int k = 0; k < 8; ++k) PR_TRY(launch_plan(L.inner, s));
+                for (int k = 0; k < 8; ++k) {
+                    PR_TRY(launch_plan(L.inner, s));
+                    if (L.f_shift) {
+                        PR_CUDA(cudaLaunchKernel(L.f_shift, dim3(L.grid_u), dim3(256), aq, 0, s));
+                        note_launch();
+                    }
+                }
                 PR_CUDA(cudaMemcpyAsync(hs, sx, 2 * sizeof(SolveState), cudaMemcpyDeviceToHost, s));
                 PR_CUDA(cudaStreamSynchronize(s));
                 if (hs[1].done) break;
@@ -376,7 +455,8 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     PR_CUDA(cudaStreamSynchronize(s));
     if (graph_loop)  // residual and update kernels per outer step, the inner sweeps
         note_launch((uint64_t)2 * hs[0].outer_iter +
-                    (uint64_t)L.inner.nlaunch * (hs[0].iter - hs[0].outer_iter));
+                    (uint64_t)(L.inner.nlaunch + (L.f_shift ? 1 : 0)) *
+                        (hs[0].iter - hs[0].outer_iter));
     pr_status st = (pr_status)hs[0].status;
     if (res) {
         res->outer_iters = hs[0].outer_iter;

@@ -377,6 +377,8 @@ static void destroy_impl(pr_graph *g)
     if (!g) return;
     cudaStream_t s = g->mem.stream;
     cudaStreamSynchronize(s);
+    destroy_impl(g->rev);
+    g->rev = nullptr;
     release_graphs(g);
     for (Buf *b : g->owned) buf_free(g, *b, s);
     cudaStreamSynchronize(s);
@@ -587,7 +589,7 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
     g->tune.hub_seg = 2048;
     g->tune.tile = 256;
     g->tune.deterministic_gs = 0;
-    g->tune.stage_kb = 0;
+    g->tune.stage_kb = 32;
     g->tune.wait_limit = 0;
     g->tune.test_stall = 0;
     pr_status st = PR_OK;

@@ -89,11 +89,12 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs)
     p.ldesc = it.desc.as<int4>() + it.nhubseg;
     p.nlt = it.nlt;
     p.lcap = it.lcap;
-    // staged copy: the room left beside the warp slices (or stage_kb KB)
+    // staged copy of stage_kb KB, at most the room left beside the warp
+    // slices (shared memory is taken from the L1 cache, which also keeps hot
+    // contributions, so a modest copy serves best)
     const Layout L0 = make_layout(p.lcap, fp64 ? 8 : 4, (int)elem, gs, 0);
     int64_t stage = ((int64_t)g->max_smem - L0.total - SWEEP_STATIC_SMEM) / (int64_t)elem;
-    if (it.stage_kb > 0) stage = std::min<int64_t>(stage, (int64_t)it.stage_kb * 1024 / elem);
-    if (it.stage_kb < 0) stage = 0;
+    stage = it.stage_kb > 0 ? std::min<int64_t>(stage, (int64_t)it.stage_kb * 1024 / elem) : 0;
     p.stage = (int32_t)std::max<int64_t>(0, std::min<int64_t>(g->n, stage));
     p.kinds = KIND_ALL;
     p.close = 1;
@@ -162,7 +163,8 @@ template pr_status make_plan<__nv_bfloat16, float>(pr_graph *, const SweepParams
                                                    SweepPlan &);
 template pr_status make_plan<__half, float>(pr_graph *, const SweepParams &, bool, SweepPlan &);
 
-pr_status add_plan_nodes(cudaGraph_t body, SweepPlan &plan, cudaGraphConditionalHandle h)
+pr_status add_plan_nodes(cudaGraph_t body, SweepPlan &plan, cudaGraphConditionalHandle h,
+                         cudaGraphNode_t *last)
 {
     cudaGraphNode_t prev = nullptr;
     for (int k = 0; k < plan.nlaunch; ++k) {
@@ -179,6 +181,7 @@ pr_status add_plan_nodes(cudaGraph_t body, SweepPlan &plan, cudaGraphConditional
         PR_CUDA(cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
         prev = node;
     }
+    if (last) *last = prev;
     return PR_OK;
 }
 
@@ -229,7 +232,7 @@ pr_status loop_graph(pr_graph *g, int key, SweepPlan &plan, cudaGraphExec_t *exe
         cudaGraphDestroy(graph);
         return cuda_status(e, "cudaGraphAddNode(while)", __FILE__, __LINE__);
     }
-    pr_status st = add_plan_nodes(cp.conditional.phGraph_out[0], plan, h);
+    pr_status st = add_plan_nodes(cp.conditional.phGraph_out[0], plan, h, nullptr);
     if (st != PR_OK) {
         cudaGraphDestroy(graph);
         return st;
@@ -419,6 +422,7 @@ extern "C" const char *pr_status_string(pr_status s)
     case PR_NOT_CONVERGED: return "not converged (max_iter reached)";
     case PR_ERR_TIMEOUT: return "device wait timed out";
     case PR_ERR_UNSUPPORTED: return "unsupported option combination";
+    case PR_ERR_NUMERIC: return "non-finite value in the iterate";
     }
     return "unknown status";
 }

@@ -34,8 +34,10 @@ struct SweepPlan {
 };
 template <typename T, typename A>
 pr_status make_plan(pr_graph *g, const SweepParams &p, bool gs, SweepPlan &plan);
-// adds the plan's launches as a chain of kernel nodes of `body`
-pr_status add_plan_nodes(cudaGraph_t body, SweepPlan &plan, cudaGraphConditionalHandle h);
+// adds the plan's launches as a chain of kernel nodes of `body` (the last
+// node in *last, if given)
+pr_status add_plan_nodes(cudaGraph_t body, SweepPlan &plan, cudaGraphConditionalHandle h,
+                         cudaGraphNode_t *last);
 // launches one sweep of the plan (no graph)
 pr_status launch_plan(SweepPlan &plan, cudaStream_t s);
 // Instantiates (or reuses) a graph: WHILE(cond) { the plan's launches }.

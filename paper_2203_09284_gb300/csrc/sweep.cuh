@@ -94,14 +94,24 @@ struct SweepParams {
     int32_t use_cond;
     int32_t renorm;               // fused sweep: rescale to sum 1
     int32_t dc;                   // correction sweep of a defect-correction solve
+    int32_t shift;                // correction sweep: restore the exact sum of e
 };
 
+// Loads of the stored vector.  Jacobi: read-only path (the kernel never
+// writes the buffer it gathers from).  Fused: plain loads, cached in L1 (the
+// buffer is updated in place by other warps; a load returns the value before
+// or after a concurrent update, both of which the fused sweep allows).
+// ld_l2 reads from L2, where a value this warp stored earlier in the sweep
+// (st_y, also through L2) is visible after a __syncwarp.
 template <typename T, bool GS>
 __device__ __forceinline__ T ld_y(const T *p, int i)
 {
-    if constexpr (GS) return __ldcg(p + i);
+    if constexpr (GS) return p[i];
     else return __ldg(p + i);
 }
+
+template <typename T>
+__device__ __forceinline__ T ld_l2(const T *p, int i) { return __ldcg(p + i); }
 
 template <typename T, bool GS>
 __device__ __forceinline__ void st_y(T *p, int i, T v)
@@ -114,7 +124,7 @@ __device__ __forceinline__ void st_y(T *p, int i, T v)
 template <>
 __device__ __forceinline__ __nv_bfloat16 ld_y<__nv_bfloat16, true>(const __nv_bfloat16 *p, int i)
 {
-    return __ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short *>(p) + i));
+    return __ushort_as_bfloat16(reinterpret_cast<const unsigned short *>(p)[i]);
 }
 template <>
 __device__ __forceinline__ __nv_bfloat16 ld_y<__nv_bfloat16, false>(const __nv_bfloat16 *p, int i)
@@ -124,12 +134,22 @@ __device__ __forceinline__ __nv_bfloat16 ld_y<__nv_bfloat16, false>(const __nv_b
 template <>
 __device__ __forceinline__ __half ld_y<__half, true>(const __half *p, int i)
 {
-    return __ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(p) + i));
+    return __ushort_as_half(reinterpret_cast<const unsigned short *>(p)[i]);
 }
 template <>
 __device__ __forceinline__ __half ld_y<__half, false>(const __half *p, int i)
 {
     return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p) + i));
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 ld_l2<__nv_bfloat16>(const __nv_bfloat16 *p, int i)
+{
+    return __ushort_as_bfloat16(__ldcg(reinterpret_cast<const unsigned short *>(p) + i));
+}
+template <>
+__device__ __forceinline__ __half ld_l2<__half>(const __half *p, int i)
+{
+    return __ushort_as_half(__ldcg(reinterpret_cast<const unsigned short *>(p) + i));
 }
 template <>
 __device__ __forceinline__ void st_y<__nv_bfloat16, true>(__nv_bfloat16 *p, int i, __nv_bfloat16 v)
@@ -309,6 +329,16 @@ __device__ __forceinline__ void close_sweep(const SweepParams &p)
         if (so->history) so->history[total - 1] = err;
         conv = err <= st->tau;
         stop = conv || it >= st->max_iter || total >= so->max_iter || error;
+        if (p.shift) {
+            // e <- e + beta x with sum(e) = mass_target afterwards; in stored
+            // units e~ += gamma Y64 (the shift kernel applies it), so the
+            // dangling mass and sum of e~ move by gamma times those of x~
+            const double beta = (st->mass_target - st->sigma * sum) / (so->sigma * so->sum);
+            const double gam = beta * so->sigma / st->sigma;
+            st->shift = gam;
+            st->dang = dang + gam * so->dang;
+            st->sum = sum + gam * so->sum;
+        }
         if (error) {
             so->error = error;
             so->status = error;
@@ -534,7 +564,7 @@ __device__ __forceinline__ void low_item(const SweepParams &p, int k, const Src<
                     // __syncwarp, so visible to this lane)
                     const int t = sidx[i];
                     if (t >= 0 && v0 + t < u0) {
-                        const A nv = to_a<A>(ld_y<T, true>(yself, v0 + t));
+                        const A nv = to_a<A>(ld_l2<T>(yself, v0 + t));
                         val = W ? ew[ea + i] * nv : nv;
                     }
                 }
@@ -596,7 +626,13 @@ __device__ __forceinline__ void run_items(const SweepParams &p, const T *yin, Fi
     const int nh = (p.kinds & KIND_HUB) ? p.nhubseg : 0;
     const int nm = (p.kinds & KIND_MID) ? p.mi[4] : 0;
     const int nl = (p.kinds & KIND_LOW) ? p.nlt : 0;
-    for (int i = gw; i < nh + nm + nl; i += nw) {
+    // round r gives warp gw item r*nw + gw (r even) or r*nw + nw-1-gw (r odd):
+    // the items' cost falls within each class, and alternating the direction
+    // keeps any warp from always taking the dearest item of a round
+    const int total = nh + nm + nl;
+    for (int r = 0;; ++r) {
+        const int i = r * nw + ((r & 1) ? nw - 1 - gw : gw);
+        if (i >= total) break;
         if (i < nh) hub_item<T, A, GS, W>(p, i, src, fin, lane);
         else if (i < nh + nm) mid_item<T, A, GS, W>(p, i - nh, src, fin, lane);
         else low_item<T, A, GS, W>(p, i - nh - nm, src, fin, lane, slice, L);
@@ -646,9 +682,9 @@ __global__ void k_sweep_serial(SweepParams p)
     for (int u = 0; u < p.n; ++u) {
         const int a = p.col_ptr[u], e = p.col_ptr[u + 1];
         A acc = 0;
-        for (int i = a + lane; i < e; i += 32) acc += to_a<A>(ld_y<T, true>(y, p.row_idx[i]));
+        for (int i = a + lane; i < e; i += 32) acc += to_a<A>(ld_l2<T>(y, p.row_idx[i]));
         acc = warp_sum(acc);
-        if (lane == 0) fin(u, acc, p.outdeg[u], inv[u], ld_y<T, true>(y, u), rhs_of<A>(p, u, fin.base()));
+        if (lane == 0) fin(u, acc, p.outdeg[u], inv[u], ld_l2<T>(y, u), rhs_of<A>(p, u, fin.base()));
         __syncwarp();
     }
     block_partials<A>(st, fin.pt);

@@ -204,7 +204,8 @@ def test_full_size_rmat22_properties():
     # certifies the error bound of the stop rule.  Jacobi's final residual is
     # d times its last successive difference; the fused sweep's is reported.
     for v, prec, limit in (("jacobi", "fp64", 0.8501e-10), ("gs", "fp64", 5e-10),
-                           ("jacobi", "fp32_dc", 1.0001e-10), ("gs", "fp32_dc", 1.0001e-10)):
+                           ("jacobi", "fp32_dc", 1.0001e-10), ("gs", "fp32_dc", 1.0001e-10),
+                           ("jacobi", "bf16_dc", 1.0001e-10), ("gs", "fp16_dc", 1.0001e-10)):
         x, r = g.solve(variant=v, precision=prec, threshold=1e-10)
         assert r.status == 0
         xs = x.cpu().numpy()
