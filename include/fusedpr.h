@@ -246,6 +246,28 @@ pr_status pr_solve_multi(pr_graph *const *graphs, int32_t G, const pr_options *o
 pr_status pr_backward(pr_graph *g, const pr_options *o, const double *x, const double *grad_x,
                       double *grad_w, double *grad_d, pr_result *res, void *stream);
 
+/*
+ * Exclusive prefix sum of int32 values without any device allocation (the
+ * paper has no counterpart: this is the offsets step of the graph build,
+ * col_ptr from in-degrees, offered for callers that must not allocate, e.g.
+ * inside a memory-capped or preallocated runtime).
+ *   in     device int32 [count] (read only; may be NULL if count == 0)
+ *   out    device int32 [count + 1]: out[i] = in[0] + ... + in[i-1],
+ *          out[count] = the total (sums must fit in int32)
+ *   count  0 <= count <= 134217728 (65536 blocks of 2048); larger counts
+ *          return PR_ERR_INVALID_ARG before any device work
+ * Scratch: the per-block totals live in one fixed 256 KB __device__ array
+ * of the library (one copy per device), located once per device with
+ * cudaGetSymbolAddress; nothing is allocated or freed.  All calls on a
+ * device share that array: calls that overlap in time (on different
+ * streams or threads) race and give wrong results, so serialise them.  The
+ * first call on a device does the one-time lookup; make it before any
+ * stream capture.  Work is ordered on `stream`; the function returns
+ * without synchronising.
+ */
+pr_status pr_scan_exclusive_noalloc(const int32_t *in, int32_t *out, int64_t count,
+                                    void *stream);
+
 /* Static string for a status code. */
 const char *pr_status_string(pr_status s);
 

@@ -24,7 +24,7 @@ __all__ = [
     "PrOptions", "PrResult", "PrTune", "PrAllocator", "PageRankError", "lib", "library_path",
     "pr_options_default", "pr_graph_create", "pr_graph_destroy", "pr_graph_info",
     "pr_graph_export", "pr_solve", "pr_solve_batched", "pr_solve_multi", "pr_backward",
-    "pr_status_string", "pr_last_error", "pr_kernel_launches", "Graph",
+    "pr_scan_exclusive_noalloc", "pr_status_string", "pr_last_error", "pr_kernel_launches", "Graph",
 ]
 
 PR_OK, PR_ERR_INVALID_ARG, PR_ERR_OOM, PR_ERR_CUDA = 0, 1, 2, 3
@@ -118,6 +118,7 @@ def lib():
                                          ctypes.POINTER(vp), ctypes.POINTER(PrResult), vp]
             L.pr_backward.argtypes = [vp, ctypes.POINTER(PrOptions), vp, vp, vp, vp,
                                       ctypes.POINTER(PrResult), vp]
+            L.pr_scan_exclusive_noalloc.argtypes = [vp, vp, i64, vp]
             L.pr_status_string.argtypes = [ctypes.c_int]
             L.pr_status_string.restype = ctypes.c_char_p
             L.pr_last_error.argtypes = []
@@ -126,7 +127,7 @@ def lib():
             L.pr_kernel_launches.restype = ctypes.c_uint64
             for name in ("pr_options_default", "pr_graph_create", "pr_graph_info",
                          "pr_graph_export", "pr_solve", "pr_solve_batched", "pr_solve_multi",
-                         "pr_backward"):
+                         "pr_backward", "pr_scan_exclusive_noalloc"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -298,6 +299,14 @@ def pr_solve_multi(handles, options, x_outs, stream=None):
     st = lib().pr_solve_multi(harr, G, ctypes.byref(options), xarr, res, _stream(stream))
     _check(st, "pr_solve_multi", ok=(PR_OK, PR_NOT_CONVERGED))
     return list(res)
+
+
+def pr_scan_exclusive_noalloc(inp, out, count=None, stream=None):
+    """out[0..count] = exclusive prefix sums of inp[0..count) (int32 device
+    tensors), using the library's fixed scratch array (no allocation)."""
+    count = int(inp.numel()) if count is None else int(count)
+    st = lib().pr_scan_exclusive_noalloc(_ptr(inp), _ptr(out), count, _stream(stream))
+    _check(st, "pr_scan_exclusive_noalloc")
 
 
 def pr_backward(handle, options, x, grad_x, grad_w=None, grad_d=None, stream=None):

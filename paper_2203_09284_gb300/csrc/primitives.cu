@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <atomic>
 
 #include "common.cuh"
@@ -180,6 +181,68 @@ pr_status scan_exclusive(pr_graph *g, const int32_t *in, int32_t *out, int64_t c
     if (e != cudaSuccess) return cuda_status(e, "scan launch", __FILE__, __LINE__);
     return PR_OK;
 }
+
+// ------------------------------------------------- scan without allocation
+// Block totals of pr_scan_exclusive_noalloc live in this fixed array (one
+// copy per device, 256 KB) instead of allocated scratch.  Every call on a
+// device uses the same array, so calls must not overlap in time.
+constexpr int64_t NOALLOC_SCAN_BLOCKS = 65536;
+static __device__ __align__(256) int32_t g_scan_blocks[NOALLOC_SCAN_BLOCKS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_scan_mu;
+static int32_t *g_scan_addr[NOALLOC_MAX_DEVICES];  // device address, per device
+
+}  // namespace fpr
+
+extern "C" pr_status pr_scan_exclusive_noalloc(const int32_t *in, int32_t *out, int64_t count,
+                                               void *stream)
+{
+    using namespace fpr;
+    if (count < 0 || !out || (count > 0 && !in)) {
+        set_error("pr_scan_exclusive_noalloc: need count >= 0, in (if count > 0) and out");
+        return PR_ERR_INVALID_ARG;
+    }
+    if (count > NOALLOC_SCAN_BLOCKS * SCAN_TILE) {
+        set_error("pr_scan_exclusive_noalloc: count %lld exceeds the limit %lld",
+                  (long long)count, (long long)(NOALLOC_SCAN_BLOCKS * SCAN_TILE));
+        return PR_ERR_INVALID_ARG;
+    }
+    int dev = -1;
+    PR_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        set_error("pr_scan_exclusive_noalloc: device %d out of range", dev);
+        return PR_ERR_UNSUPPORTED;
+    }
+    int32_t *scratch;
+    {
+        std::lock_guard<std::mutex> lock(g_scan_mu);
+        if (!g_scan_addr[dev]) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_scan_blocks);
+            if (e != cudaSuccess)
+                return cuda_status(e, "cudaGetSymbolAddress(scan scratch)", __FILE__, __LINE__);
+            g_scan_addr[dev] = static_cast<int32_t *>(p);
+        }
+        scratch = g_scan_addr[dev];
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t nb = (count + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb == 0) {
+        PR_CUDA(cudaMemsetAsync(out, 0, sizeof(int32_t), s));
+        return PR_OK;
+    }
+    k_scan_reduce<<<(unsigned)nb, SCAN_BS, 0, s>>>(in, count, scratch);
+    note_launch();
+    k_scan_spine<<<1, 1024, 0, s>>>(scratch, nb, out + count);
+    note_launch();
+    k_scan_down<<<(unsigned)nb, SCAN_BS, 0, s>>>(in, out, count, scratch);
+    note_launch();
+    PR_CUDA(cudaGetLastError());
+    return PR_OK;
+}
+
+namespace fpr {
 
 // ------------------------------------------------------------- degrees
 // Out/in-degree histograms with warp-aggregated atomics (R-MAT hubs put many
