@@ -37,6 +37,31 @@ sys.path.insert(0, ROOT)
 METRIC = "R-MAT-22 time to L1<1e-10 and GTEPS (% HBM peak), mixed/fused vs plain FP64"
 
 
+# DRAM bytes (read + write) of one k_sweep<float, float, 0, 0> launch of the
+# workload, from the ncu capture summarised in profiles/ (see the command
+# there); reported only while the sweep's sources are the ones captured.
+SWEEP_TRAFFIC = {
+    "sources_sha256": "e31b149fbe665452d0ddba77c368285e87c45d26a39a30d8868cd153cb4c3750",
+    "bytes": 343650560,  # 339,242,496 read + 4,408,064 written
+}
+SWEEP_SOURCES = ("sweep.cuh", "tma.cuh", "common.cuh")
+
+
+def sweep_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for name in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_09284_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def sweep_traffic():
+    if SWEEP_TRAFFIC["sources_sha256"] and SWEEP_TRAFFIC["sources_sha256"] == sweep_sources_sha256():
+        return SWEEP_TRAFFIC["bytes"]
+    return None
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -112,6 +137,88 @@ def b_alg(n, m, prec):
     gathered vector once (s_g n) and the rank read and write (2 s_x n)."""
     s = {"fp64": 8, "fp32": 4, "fp32_dc": 4, "bf16_dc": 2, "fp16_dc": 2}[prec]
     return 4 * m + 4 * (n + 1) + 3 * s * n
+
+
+def measure_rows(dev, stream, peak, timed):
+    """The other rows of the hot path, each timed with CUDA events on its
+    stream (outside the headline step): batched personalised PageRank at
+    R-MAT scale 20 with 256 teleports, 64 uneven graphs solved together, and
+    the adjoint with gradients at scale 18."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2203_09284_gb300 as fp
+    rows = {}
+
+    # batched PPR: one-hot teleports, L1 change <= 1e-8 per column
+    n, s_h, d_h = gen.rmat(20, 16, seed=4)
+    m = len(s_h)
+    g = fp.Graph(n, torch.from_numpy(s_h).to(dev), torch.from_numpy(d_h).to(dev))
+    seeds = torch.from_numpy(gen.seed_vertices(256, n, seed=1)).to(dev)
+    row = {"workload": "rmat20_ef16_seed4_B256_onehot", "n": n, "edges": m, "threshold": 1e-8}
+    for prec in ("fp32", "fp64"):
+        ms, (X, res) = timed(lambda: g.solve_batched(seeds, threshold=1e-8, precision=prec), 2)
+        t1, _ = timed(lambda: g.solve_batched(seeds, threshold=0.0, max_iter=1, precision=prec), 2)
+        t9, _ = timed(lambda: g.solve_batched(seeds, threshold=0.0, max_iter=9, precision=prec), 2)
+        sweep_ms = (t9 - t1) / 8
+        sweeps = max(r.iters for r in res)
+        elem = 4 if prec == "fp32" else 8
+        # every gathered row is a full B-wide read: E x B x elem per sweep
+        gathered = m * 256 * elem
+        row[prec] = {"ms": round(ms, 3), "sweeps": sweeps,
+                     "converged": int(sum(r.status == 0 for r in res)),
+                     "sweep_us": round(sweep_ms * 1e3, 1),
+                     "row_gather_GBps": round(gathered / (sweep_ms * 1e-3) / 1e9, 1),
+                     "frac_of_hbm": round(gathered / (sweep_ms * 1e-3) / 1e9 / peak, 3),
+                     "teps_x_columns_G": round(m * 256 * sweeps / (ms * 1e-3) / 1e9, 1)}
+    ms64, _ = timed(lambda: g.solve(threshold=1e-8), 2)
+    row["single_vector_fp64_ms"] = round(ms64, 3)
+    g.close()
+    rows["batched_ppr"] = row
+
+    # 64 uneven graphs in one solve
+    shapes = gen.multi_graph_shapes(64, seed=1)
+    graphs, E = [], 0
+    for i, (sc, ef) in enumerate(shapes):
+        nn, ss, dd = gen.rmat(sc, ef, seed=1000 + i)
+        E += len(ss)
+        graphs.append(fp.Graph(nn, torch.from_numpy(ss).to(dev), torch.from_numpy(dd).to(dev)))
+    row = {"workload": "64 rmat graphs, scale 10-18, ef 8-32, seed 1", "edges": E}
+    for prec, thr in (("fp64", 1e-10), ("fp32", 1e-6)):
+        ms, (xs, res) = timed(lambda: fp.solve_multi(graphs, threshold=thr, precision=prec), 2)
+        seq = 0.0
+        for gg in graphs:
+            t_, _ = timed(lambda: gg.solve(threshold=thr, precision=prec), 1)
+            seq += t_
+        sweeps = sum(r.iters for r in res)
+        row[prec] = {"threshold": thr, "ms": round(ms, 3), "one_by_one_ms": round(seq, 3),
+                     "max_sweeps": max(r.iters for r in res),
+                     "gteps": round(sum(r.iters * gg.m for r, gg in zip(res, graphs))
+                                    / (ms * 1e-3) / 1e9, 1)}
+        del sweeps
+    for gg in graphs:
+        gg.close()
+    rows["multi_graph"] = row
+
+    # adjoint and gradients, weighted graph, 1,000 loss targets
+    n, s_h, d_h = gen.rmat(18, 16, seed=18)
+    w = torch.from_numpy(gen.edge_weights(len(s_h), seed=18)).to(dev)
+    g = fp.Graph(n, torch.from_numpy(s_h).to(dev), torch.from_numpy(d_h).to(dev), w=w)
+    xg, _ = g.solve(threshold=1e-12)
+    t_, c_ = gen.loss_targets(1000, n, 18)
+    gx = np.zeros(n)
+    gx[t_] = c_
+    gx = torch.from_numpy(gx).to(dev)
+    row = {"workload": "rmat18_ef16_seed18_weighted_1000targets", "n": n, "edges": len(s_h)}
+    for prec, thr in (("fp64", 1e-12), ("fp32", 1e-8)):
+        ms, (gw, gd, r) = timed(lambda: g.backward(xg, gx, precision=prec, threshold=thr), 2)
+        fms, (_, fr) = timed(lambda: g.solve(threshold=thr, precision=prec), 2)
+        row[prec] = {"threshold": thr, "backward_ms": round(ms, 3), "adjoint_sweeps": r.iters,
+                     "forward_ms": round(fms, 3), "forward_sweeps": fr.iters}
+    g.close()
+    rows["adjoint"] = row
+    return rows
 
 
 def run_ours(args, rank, world):
@@ -199,11 +306,11 @@ def run_ours(args, rank, world):
     # events around back-to-back launches of the device loop
     sweep_prec = {"fp32_dc": "fp32", "bf16_dc": "fp32", "fp16_dc": "fp32"}.get(args.precision,
                                                                              args.precision)
-    k_long, k_short = 41, 1
+    k_long, k_short = 101, 1
     t_long, _ = timed(lambda: g.solve(out=x_out[0], variant="jacobi", precision=sweep_prec,
-                                      threshold=0.0, max_iter=k_long))
+                                      threshold=0.0, max_iter=k_long), 5)
     t_short, _ = timed(lambda: g.solve(out=x_out[0], variant="jacobi", precision=sweep_prec,
-                                       threshold=0.0, max_iter=k_short))
+                                       threshold=0.0, max_iter=k_short), 5)
     sweep_ms = (t_long - t_short) / (k_long - k_short)
     alg = b_alg(n, m, sweep_prec)
     peaks = _peaks()
@@ -211,8 +318,9 @@ def run_ours(args, rank, world):
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
     achieved = alg / (sweep_ms * 1e-3) / 1e9
+    traffic = args.traffic if args.traffic is not None else sweep_traffic()
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": args.traffic,
+                "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": f"k_sweep<{sweep_prec}, jacobi>", "sweep_us": round(sweep_ms * 1e3, 2),
                 "alg_bytes_per_sweep": alg, "peak_source": peak_src}
 
@@ -248,6 +356,7 @@ def run_ours(args, rank, world):
            "unit": "GTEPS", "h2d_bytes_per_step": 8 * m,
            "d2h_bytes_per_step": 8 * n * len(variants), "ms_per_step": round(e2e_ms, 3)}
     g.close()
+    rows = None if args.no_rows else measure_rows(dev, stream, peak, timed)
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "GTEPS", "n_gpus": world,
@@ -266,6 +375,8 @@ def run_ours(args, rank, world):
         "gpu_launches": int(launches),
         "roofline": roofline, "e2e": e2e, "clocks": clk.summary(),
     }
+    if rows is not None:
+        out["rows"] = rows
     return out
 
 
@@ -303,6 +414,8 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per sweep launch from an ncu capture (reported as is)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the batched, multi-graph and adjoint measurements")
     ap.add_argument("--mode", default="bench", choices=["bench", "sweeps"],
                     help="sweeps: only build the workload graph and run --sweeps plain "
                          "sweeps as separate launches (for profiler captures)")

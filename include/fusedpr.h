@@ -89,11 +89,11 @@ typedef struct {
  * (in-degree descending), where the in-degree bins are contiguous. */
 typedef struct {
     int32_t t_lo;      /* in-degree <= t_lo: low-degree tiles, one lane per
-                          vertex (default 16, at most 32) */
+                          vertex (default 32, at most 32) */
     int32_t t_hub;     /* in-degree >  t_hub: hub, split into segments of
                           hub_seg in-edges, a warp per segment (default
-                          1024); in between: 4 to 32 lanes per vertex */
-    int32_t hub_seg;   /* in-edges per hub segment (default 2048, 256 to
+                          4096); in between: 4 to 32 lanes per vertex */
+    int32_t hub_seg;   /* in-edges per hub segment (default 4096, 256 to
                           8192) */
     int32_t tile;      /* work units (in-edges + vertices) per low-degree
                           tile, whose in-edges a warp gathers into shared
@@ -103,7 +103,7 @@ typedef struct {
     int32_t stage_kb;  /* shared memory (KB) per block for a copy of the
                           stored vector's first entries, the most-gathered
                           contributions in the degree-ordered ids (0:
-                          the default, 32; -1: none; > 0: that many KB, at
+                          the default, 64; -1: none; > 0: that many KB, at
                           most the room the tiles leave) */
     int32_t wait_limit;/* polls of a copy barrier before a device-side wait
                           gives up with PR_ERR_TIMEOUT (0: 4M) */

@@ -102,7 +102,7 @@ struct AdjFin {
 };
 
 template <typename T, typename A>
-__global__ void __launch_bounds__(SWEEP_BS, 1) k_adj_sweep(SweepParams p)
+__global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_adj_sweep(SweepParams p)
 {
     SolveState *st = p.st;
     if (st->done) {

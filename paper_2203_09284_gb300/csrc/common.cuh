@@ -127,10 +127,10 @@ struct Items {
     Buf hubseg_start;             // [nhub + 1] first segment of each hub
     Buf seg_acc;                  // [nhubseg] double partial sums
     Buf hub_cnt;                  // [nhub] segments finished this sweep
-    Buf desc;                     // [nhubseg + nlt] int4: hub segments
-                                  // {hub, 0, ea, eb}, then low tiles
-                                  // {v0, v1, ea, eb}: vertices [v0, v1),
-                                  // in-list slots [ea, eb)
+    Buf desc;                     // [nhubseg + mi[4] + nlt] int4: hub
+                                  // segments {hub, 0, ea, eb}, then mid
+                                  // groups and low tiles {v0, v1, ea, eb}:
+                                  // vertices [v0, v1), in-list slots [ea, eb)
 };
 
 }  // namespace fpr

@@ -110,7 +110,7 @@ __device__ __forceinline__ double fp16_scale(double rnorm, double d)
 }
 
 template <typename Te, bool W>
-__global__ void __launch_bounds__(SWEEP_BS, 1) k_dc_resid(DCParams q)
+__global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_dc_resid(DCParams q)
 {
     SolveState *sx = q.sx, *se = q.se;
     if (sx->done) {

@@ -131,14 +131,30 @@ __global__ void k_tile_starts(int32_t ntiles, int32_t first, int32_t n,
     tile_start[k] = lo;
 }
 
-// Item descriptors: hub segments {hub, 0, ea, eb} first, then low tiles
-// {v0, v1, ea, eb}.
+struct MidRanges {
+    int32_t mb[5], mi[5];
+};
+
+// Item descriptors in item order: hub segments {hub, 0, ea, eb}, mid groups
+// (32 >> k lanes per vertex, 1 << k vertices of sub-range k) and low tiles,
+// both {v0, v1, ea, eb}.
 __global__ void k_item_desc(int32_t nhubseg, int32_t nhub, const int32_t *__restrict__ hubseg_start,
-                            int hub_seg, int32_t ntiles, const int32_t *__restrict__ tile_start,
+                            int hub_seg, MidRanges mr, int32_t ntiles,
+                            const int32_t *__restrict__ tile_start,
                             const int32_t *__restrict__ col_ptr, int4 *desc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nhubseg + ntiles) return;
+    const int nmid = mr.mi[4];
+    if (i >= nhubseg + nmid + ntiles) return;
+    if (i >= nhubseg && i < nhubseg + nmid) {
+        const int j = i - nhubseg;
+        int k = 0;
+        while (k < 3 && j >= mr.mi[k + 1]) ++k;
+        const int v0 = mr.mb[k] + (j - mr.mi[k]) * (1 << k);
+        const int v1 = min(v0 + (1 << k), mr.mb[k + 1]);
+        desc[i] = make_int4(v0, v1, col_ptr[v0], col_ptr[v1]);
+        return;
+    }
     if (i < nhubseg) {
         int lo = 0, hi = nhub - 1;  // hub owning segment i
         while (lo < hi) {
@@ -150,7 +166,7 @@ __global__ void k_item_desc(int32_t nhubseg, int32_t nhub, const int32_t *__rest
         const int a = col_ptr[h] + (i - hubseg_start[h]) * hub_seg;
         desc[i] = make_int4(h, 0, a, min(a + hub_seg, col_ptr[h + 1]));
     } else {
-        const int k = i - nhubseg;
+        const int k = i - nhubseg - nmid;
         const int v0 = tile_start[k], v1 = tile_start[k + 1];
         desc[i] = make_int4(v0, v1, col_ptr[v0], col_ptr[v1]);
     }
@@ -275,11 +291,16 @@ pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
     k_tile_starts<<<(it.nlt + 256) / 256, 256, 0, s>>>(it.nlt, first, n, rcp, t.tile,
                                                        tile_start.as<int32_t>());
     note_launch();
-    const int nitems = it.nhubseg + it.nlt;
+    const int nitems = it.nhubseg + it.mi[4] + it.nlt;
     PR_TRY(buf_alloc(g, it.desc, sizeof(int4) * (size_t)std::max(nitems, 1), s));
     if (nitems > 0) {
+        MidRanges mr;
+        for (int k = 0; k < 5; ++k) {
+            mr.mb[k] = it.mb[k];
+            mr.mi[k] = it.mi[k];
+        }
         k_item_desc<<<(nitems + 255) / 256, 256, 0, s>>>(
-            it.nhubseg, it.nhub, it.hubseg_start.as<int32_t>(), t.hub_seg, it.nlt,
+            it.nhubseg, it.nhub, it.hubseg_start.as<int32_t>(), t.hub_seg, mr, it.nlt,
             tile_start.as<int32_t>(), rcp, it.desc.as<int4>());
         note_launch();
     }
@@ -584,12 +605,12 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
         g->mem.hooks = *alloc;
         g->mem.has_hooks = true;
     }
-    g->tune.t_lo = 16;
-    g->tune.t_hub = 1024;
-    g->tune.hub_seg = 2048;
+    g->tune.t_lo = 32;
+    g->tune.t_hub = 4096;
+    g->tune.hub_seg = 4096;
     g->tune.tile = 256;
     g->tune.deterministic_gs = 0;
-    g->tune.stage_kb = 32;
+    g->tune.stage_kb = 64;
     g->tune.wait_limit = 0;
     g->tune.test_stall = 0;
     pr_status st = PR_OK;

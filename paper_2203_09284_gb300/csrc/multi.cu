@@ -46,9 +46,10 @@ __device__ __forceinline__ void multi_item(const SweepParams &p, int j, int lane
     SweepFin<T, A, false, W> fin(p, load_ctx<A>(st), yout);
     const Src<T, false> src{yin, nullptr, 0};
     const int nh = p.nhubseg, nm = p.mi[4];
-    if (j < nh) hub_item<T, A, false, W>(p, j, src, fin, lane);
-    else if (j < nh + nm) mid_item<T, A, false, W>(p, j - nh, src, fin, lane);
-    else low_item<T, A, false, W>(p, j - nh - nm, src, fin, lane, slice, L);
+    const int4 d = __ldg(p.desc + j);
+    if (j < nh) hub_item<T, A, false, W>(p, j, d, src, fin, lane);
+    else if (j < nh + nm) mid_item<T, A, false, W>(p, j - nh, d, src, fin, lane);
+    else low_item<T, A, false, W>(p, d, src, fin, lane, slice, L);
     // this item's sums, then the item count; the last item closes the sweep
     const double l1 = warp_sum(static_cast<double>(fin.pt.l1));
     const double lm = warp_max(static_cast<double>(fin.pt.lmax));
@@ -68,7 +69,7 @@ __device__ __forceinline__ void multi_item(const SweepParams &p, int j, int lane
 }
 
 template <typename T, typename A>
-__global__ void __launch_bounds__(SWEEP_BS, 1) k_multi_sweep(MultiParams mp)
+__global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_multi_sweep(MultiParams mp)
 {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     __shared__ bool is_last;
@@ -129,7 +130,6 @@ static pr_status solve_multi(pr_graph *const *graphs, int32_t G, const pr_option
         SweepParams &p = hp[(size_t)k];
         fill_params(g, p, fp64, sizeof(T), false);
         p.stage = 0;
-        p.kinds = KIND_ALL;
         p.close = 1;
         p.use_cond = 0;
         lcap = std::max(lcap, p.lcap);

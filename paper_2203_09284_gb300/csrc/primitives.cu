@@ -274,7 +274,8 @@ __global__ void k_degrees(int64_t m, const int32_t *__restrict__ src,
 // Stable LSD radix sort of (64-bit key, int32 value) pairs, 8 bits a pass.
 // A block owns a tile of 4096 pairs; warp w owns the w-th 512-pair run and
 // ranks it in 16 rounds of 32 with __match_any_sync, so the order within a
-// tile is preserved.
+// tile is preserved; the tile is reordered by digit in shared memory before
+// it is written out.
 constexpr int RS_BS = 256;
 constexpr int RS_ROUNDS = 16;
 constexpr int RS_TILE = RS_BS * RS_ROUNDS;
@@ -296,17 +297,31 @@ __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t m, int s
     counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = hist[threadIdx.x];
 }
 
+// Ranks the tile's pairs by digit (stable), reorders them in shared memory,
+// then writes each digit's run to its place in the output, so consecutive
+// threads store consecutive addresses.
+struct RadixSmem {
+    uint64_t k[RS_TILE];
+    int32_t v[RS_TILE];
+    int wcnt[RS_WARPS][256];
+    int bstart[256];
+    int sw[33];
+};
+
 __global__ void __launch_bounds__(RS_BS) k_radix_scatter(
     const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     int32_t *__restrict__ vout, int64_t m, int shift, const int32_t *__restrict__ offsets,
     int nblocks)
 {
-    __shared__ int wcnt[RS_WARPS][256];
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    RadixSmem &sm = *reinterpret_cast<RadixSmem *>(rs_smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_BS) (&wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_BS) (&sm.wcnt[0][0])[i] = 0;
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)warp * (RS_ROUNDS * 32);
+    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t base = tile0 + (int64_t)warp * (RS_ROUNDS * 32);
+    const int nvalid = (int)min((int64_t)RS_TILE, m - tile0);
     uint64_t k[RS_ROUNDS];
     int32_t v[RS_ROUNDS];
     int rank[RS_ROUNDS];
@@ -323,31 +338,40 @@ __global__ void __launch_bounds__(RS_BS) k_radix_scatter(
         if (valid) {
             peers = __match_any_sync(vmask, dg);
             r = __popc(peers & lt);
-            before = wcnt[warp][dg];
+            before = sm.wcnt[warp][dg];
         }
         __syncwarp();
-        if (valid && r == 0) wcnt[warp][dg] = before + __popc(peers);
+        if (valid && r == 0) sm.wcnt[warp][dg] = before + __popc(peers);
         __syncwarp();
         rank[j] = valid ? before + r : -1;
     }
     __syncthreads();
-    {   // exclusive prefix over warps for digit threadIdx.x
+    {   // exclusive prefix over warps for digit threadIdx.x, then over digits
         int run = 0;
 #pragma unroll
         for (int w = 0; w < RS_WARPS; ++w) {
-            int t = wcnt[w][threadIdx.x];
-            wcnt[w][threadIdx.x] = run;
+            int t = sm.wcnt[w][threadIdx.x];
+            sm.wcnt[w][threadIdx.x] = run;
             run += t;
         }
+        sm.bstart[threadIdx.x] = block_exclusive_sum(run, sm.sw, nullptr);
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < RS_ROUNDS; ++j) {
         if (rank[j] < 0) continue;
-        int dg = (int)((k[j] >> shift) & 0xFF);
-        int64_t pos = (int64_t)offsets[(int64_t)dg * nblocks + blockIdx.x] + wcnt[warp][dg] + rank[j];
-        kout[pos] = k[j];
-        vout[pos] = v[j];
+        const int dg = (int)((k[j] >> shift) & 0xFF);
+        const int q = sm.bstart[dg] + sm.wcnt[warp][dg] + rank[j];
+        sm.k[q] = k[j];
+        sm.v[q] = v[j];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nvalid; q += RS_BS) {
+        const uint64_t kk = sm.k[q];
+        const int dg = (int)((kk >> shift) & 0xFF);
+        const int64_t pos = (int64_t)offsets[(int64_t)dg * nblocks + blockIdx.x] + (q - sm.bstart[dg]);
+        kout[pos] = kk;
+        vout[pos] = sm.v[q];
     }
 }
 
@@ -362,6 +386,10 @@ pr_status radix_sort(pr_graph *g, uint64_t *keys, int32_t *vals, uint64_t *alt_k
     int64_t ncount = (int64_t)256 * nblocks;
     Buf counts;
     PR_TRY(buf_alloc(g, counts, sizeof(int32_t) * (size_t)(ncount + 1), s));
+    static_assert(sizeof(RadixSmem) <= 96 * 1024, "radix tile exceeds shared memory");
+    PR_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_radix_scatter),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(RadixSmem)));
     uint64_t *ka = keys, *kb = alt_k;
     int32_t *va = vals, *vb = alt_v;
     pr_status st = PR_OK;
@@ -369,8 +397,9 @@ pr_status radix_sort(pr_graph *g, uint64_t *keys, int32_t *vals, uint64_t *alt_k
         k_radix_hist<<<nblocks, RS_BS, 0, s>>>(ka, m, sh, counts.as<int32_t>(), nblocks); note_launch();
         st = scan_exclusive(g, counts.as<int32_t>(), counts.as<int32_t>(), ncount, s);
         if (st != PR_OK) break;
-        k_radix_scatter<<<nblocks, RS_BS, 0, s>>>(ka, va, kb, vb, m, sh, counts.as<int32_t>(),
-                                                  nblocks); note_launch();
+        k_radix_scatter<<<nblocks, RS_BS, sizeof(RadixSmem), s>>>(ka, va, kb, vb, m, sh,
+                                                                  counts.as<int32_t>(), nblocks);
+        note_launch();
         std::swap(ka, kb);
         std::swap(va, vb);
     }

@@ -77,7 +77,7 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs)
     p.inv = fp64 ? g->r_inv64.p : g->r_inv32.p;
     p.ew = g->weighted ? (fp64 ? g->p64_csc.p : g->p32_csc.p) : nullptr;
     p.nhub = it.nhub;
-    p.hdesc = it.desc.as<int4>();
+    p.desc = it.desc.as<int4>();
     p.nhubseg = it.nhubseg;
     p.hubseg_start = it.hubseg_start.as<int32_t>();
     p.seg_acc = it.seg_acc.as<double>();
@@ -86,7 +86,6 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs)
         p.mb[k] = it.mb[k];
         p.mi[k] = it.mi[k];
     }
-    p.ldesc = it.desc.as<int4>() + it.nhubseg;
     p.nlt = it.nlt;
     p.lcap = it.lcap;
     // staged copy of stage_kb KB, at most the room left beside the warp
@@ -96,7 +95,8 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs)
     int64_t stage = ((int64_t)g->max_smem - L0.total - SWEEP_STATIC_SMEM) / (int64_t)elem;
     stage = it.stage_kb > 0 ? std::min<int64_t>(stage, (int64_t)it.stage_kb * 1024 / elem) : 0;
     p.stage = (int32_t)std::max<int64_t>(0, std::min<int64_t>(g->n, stage));
-    p.kinds = KIND_ALL;
+    p.item_lo = 0;
+    p.item_hi = it.nhubseg + it.mi[4] + it.nlt;
     p.close = 1;
     p.wait_limit = (uint32_t)it.wait_limit;
     p.test_stall = it.test_stall;
@@ -105,8 +105,9 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs)
     p.st = g->state.as<SolveState>();
 }
 
-// One persistent block of SWEEP_BS threads per SM (fewer if there are fewer
-// items than warps); 0 with the error set if the shared memory does not fit.
+// SWEEP_MINB persistent blocks of SWEEP_BS threads per SM (fewer if there are
+// fewer items than warps); 0 with the error set if the shared memory does
+// not fit.
 unsigned sweep_grid(const pr_graph *g, int nitems, const void *func, size_t smem)
 {
     if (smem + SWEEP_STATIC_SMEM > (size_t)g->max_smem) {
@@ -116,7 +117,7 @@ unsigned sweep_grid(const pr_graph *g, int nitems, const void *func, size_t smem
         return 0;
     }
     cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int grid = std::min((nitems + SWEEP_WARPS - 1) / SWEEP_WARPS, g->num_sms);
+    const int grid = std::min((nitems + SWEEP_WARPS - 1) / SWEEP_WARPS, g->num_sms * SWEEP_MINB);
     return (unsigned)std::max(grid, 1);
 }
 
@@ -135,23 +136,29 @@ pr_status make_plan(pr_graph *g, const SweepParams &p, bool gs, SweepPlan &plan)
 {
     plan.func = pick_sweep<T, A>(gs, p.ew != nullptr);
     plan.smem = gs ? layout_of<T, A, true>(p).total : layout_of<T, A, false>(p).total;
-    const int nmid_items = p.mi[4];
-    if (gs && p.nhubseg > 0) {
+    // fused sweep: the hottest items (hub segments and the widest mid
+    // groups) first, so the rest reads their new values
+    const int total = p.nhubseg + p.mi[4] + p.nlt;
+    const int split = p.nhubseg + p.mi[1];
+    if (gs && split > 0 && split < total) {
         plan.nlaunch = 2;
         plan.p[0] = p;
-        plan.p[0].kinds = KIND_HUB;
+        plan.p[0].item_lo = 0;
+        plan.p[0].item_hi = split;
         plan.p[0].close = 0;
         plan.p[1] = p;
-        plan.p[1].kinds = KIND_MID | KIND_LOW;
+        plan.p[1].item_lo = split;
+        plan.p[1].item_hi = total;
         plan.p[1].close = 1;
-        plan.grid[0] = sweep_grid(g, p.nhubseg, plan.func, plan.smem);
-        plan.grid[1] = sweep_grid(g, nmid_items + p.nlt, plan.func, plan.smem);
+        plan.grid[0] = sweep_grid(g, split, plan.func, plan.smem);
+        plan.grid[1] = sweep_grid(g, total - split, plan.func, plan.smem);
     } else {
         plan.nlaunch = 1;
         plan.p[0] = p;
-        plan.p[0].kinds = KIND_ALL;
+        plan.p[0].item_lo = 0;
+        plan.p[0].item_hi = total;
         plan.p[0].close = 1;
-        plan.grid[0] = sweep_grid(g, p.nhubseg + nmid_items + p.nlt, plan.func, plan.smem);
+        plan.grid[0] = sweep_grid(g, total, plan.func, plan.smem);
         plan.grid[1] = 1;
     }
     if (plan.grid[0] == 0 || plan.grid[1] == 0) return PR_ERR_INVALID_ARG;

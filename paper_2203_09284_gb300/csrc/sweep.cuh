@@ -42,12 +42,12 @@
 // defect-correction forms.
 //
 // Jacobi (Algorithm 1, Eq. 2): reads y[iter & 1], writes the other buffer.
-// Fused (Algorithm 2, Eq. 9): one buffer updated in place with L2-coherent
-// loads and stores, so a vertex sees whichever contribution is there (new if
-// its in-neighbour was already updated in this sweep).  The hubs are updated
-// by a first launch, so the second launch's shared-memory copy already holds
-// their new values; inside a low tile, a vertex reads the new values of the
-// tile's earlier vertices from shared memory.  After each fused sweep the
+// Fused (Algorithm 2, Eq. 9): one buffer updated in place, so a vertex sees
+// whichever contribution is there (new if its in-neighbour was already
+// updated in this sweep).  The hottest vertices (hubs and the mid vertices
+// with more than 128 in-edges) are updated by a first launch, so the second
+// launch's shared-memory copy and loads already see their new values; inside
+// a low tile, a vertex reads the new values of the tile's earlier vertices.  After each fused sweep the
 // iterate is rescaled to sum 1 by folding 1/sum into sigma.
 #pragma once
 
@@ -56,11 +56,17 @@
 
 namespace fpr {
 
-constexpr int SWEEP_BS = 1024;
+#ifndef SWEEP_THREADS
+#define SWEEP_THREADS 1024
+#endif
+#ifndef SWEEP_BLOCKS_PER_SM
+#define SWEEP_BLOCKS_PER_SM 1
+#endif
+constexpr int SWEEP_BS = SWEEP_THREADS;          // threads per sweep block
+constexpr int SWEEP_MINB = SWEEP_BLOCKS_PER_SM;  // resident sweep blocks per SM
 constexpr int SWEEP_WARPS = SWEEP_BS / 32;
 constexpr uint32_t DEFAULT_WAIT_LIMIT = 1u << 22;
 
-enum : int32_t { KIND_HUB = 1, KIND_MID = 2, KIND_LOW = 4, KIND_ALL = 7 };
 
 struct SweepParams {
     int32_t n;
@@ -70,7 +76,10 @@ struct SweepParams {
     const void *inv;              // A[n]: 1/outdeg in the arithmetic type
     const void *ew;               // A[m]: P per in-list slot (weighted) or null
     int32_t nhub;                 // hubs are [0, nhub)
-    const int4 *hdesc;            // [nhubseg] {hub, 0, first slot, end slot}
+    const int4 *desc;             // [nhubseg + mi[4] + nlt] item descriptors, in
+                                  // item order: hub segments {hub, 0, ea, eb},
+                                  // mid groups and low tiles {v0, v1, ea, eb}
+                                  // (vertices [v0, v1), in-list slots [ea, eb))
     int32_t nhubseg;
     const int32_t *hubseg_start;  // [nhub + 1]
     double *seg_acc;              // [nhubseg]
@@ -78,11 +87,10 @@ struct SweepParams {
     int32_t mb[5];                // mid sub-range k = [mb[k], mb[k+1]): 32 >> k
                                   // lanes per vertex
     int32_t mi[5];                // items before sub-range k (mi[4]: all mid items)
-    const int4 *ldesc;            // [nlt] low tiles {v0, v1, first slot, end slot}
     int32_t nlt;
     int32_t lcap;                 // per-warp slots for a low tile's in-edges
     int32_t stage;                // y[0, stage) is copied to shared memory
-    int32_t kinds;                // items of this launch (KIND_* bits)
+    int32_t item_lo, item_hi;     // this launch's items [item_lo, item_hi)
     int32_t close;                // this launch closes the sweep
     uint32_t wait_limit;
     int32_t test_stall;
@@ -160,6 +168,24 @@ template <>
 __device__ __forceinline__ void st_y<__half, true>(__half *p, int i, __half v)
 {
     __stcg(reinterpret_cast<unsigned short *>(p) + i, __half_as_ushort(v));
+}
+
+// Cache policy of the index stream: each in-list slot is read once per
+// sweep, so it is kept out of L1 and leaves L2 first (the gathered vector,
+// reused, stays).
+__device__ __forceinline__ uint64_t policy_stream()
+{
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ int4 ld_idx4(const int32_t *p, uint64_t pol)
+{
+    int4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p), "l"(pol));
+    return r;
 }
 
 template <typename A, typename T>
@@ -401,11 +427,11 @@ __device__ __forceinline__ A group_stream(const SweepParams &p, const Src<T, GS>
 {
     A acc = 0;
     const A *ew = static_cast<const A *>(p.ew);
+    const uint64_t pol = policy_stream();
     for (int j0 = (a & ~3) + 4 * gl; j0 < e; j0 += 8 * G) {
         const int j1 = j0 + 4 * G;
-        const int4 q0 = __ldg(reinterpret_cast<const int4 *>(p.row_idx + j0));
-        const int4 q1 = j1 < e ? __ldg(reinterpret_cast<const int4 *>(p.row_idx + j1))
-                               : make_int4(0, 0, 0, 0);
+        const int4 q0 = ld_idx4(p.row_idx + j0, pol);
+        const int4 q1 = j1 < e ? ld_idx4(p.row_idx + j1, pol) : make_int4(0, 0, 0, 0);
         const int v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
         A got[8];
 #pragma unroll
@@ -439,10 +465,9 @@ __device__ __forceinline__ A rhs_of(const SweepParams &p, int u, A base)
 
 // hub segment i (one warp)
 template <typename T, typename A, bool GS, bool W, typename Fin>
-__device__ __forceinline__ void hub_item(const SweepParams &p, int i, const Src<T, GS> &src,
-                                         Fin &fin, int lane)
+__device__ __forceinline__ void hub_item(const SweepParams &p, int i, const int4 &d,
+                                         const Src<T, GS> &src, Fin &fin, int lane)
 {
-    const int4 d = __ldg(p.hdesc + i);
     const int h = d.x;
     A acc = group_stream<32, T, A, GS, W>(p, src, d.z, d.w, lane);
     const double s = warp_sum(static_cast<double>(acc));
@@ -479,7 +504,7 @@ __device__ __forceinline__ void mid_group(const SweepParams &p, int v0, int v_en
         e = __ldg(p.col_ptr + u + 1);
         if (gl == 0) {  // the epilogue's inputs, issued before the gathers
             od = __ldg(p.outdeg + u);
-            inv = static_cast<const A *>(p.inv)[u];
+            inv = __ldg(static_cast<const A *>(p.inv) + u);
             yo = ld_y<T, GS>(src.y, u);
             r = rhs_of<A>(p, u, fin.base());
         }
@@ -492,11 +517,10 @@ __device__ __forceinline__ void mid_group(const SweepParams &p, int v0, int v_en
 // low tile k (one warp): in-edges gathered into the warp's shared slice,
 // then one lane per vertex
 template <typename T, typename A, bool GS, bool W, typename Fin>
-__device__ __forceinline__ void low_item(const SweepParams &p, int k, const Src<T, GS> &src,
-                                         Fin &fin, int lane, unsigned char *slice,
-                                         const Layout &L)
+__device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
+                                         const Src<T, GS> &src, Fin &fin, int lane,
+                                         unsigned char *slice, const Layout &L)
 {
-    const int4 d = __ldg(p.ldesc + k);
     const int v0 = d.x, v1 = d.y, ea = d.z, eb = d.w;
     A *vals = reinterpret_cast<A *>(slice + L.wvals);
     short *sidx = reinterpret_cast<short *>(slice + L.wsidx);
@@ -510,16 +534,16 @@ __device__ __forceinline__ void low_item(const SweepParams &p, int k, const Src<
         a0 = __ldg(p.col_ptr + u);
         e0 = __ldg(p.col_ptr + u + 1);
         od0 = __ldg(p.outdeg + u);
-        inv0 = static_cast<const A *>(p.inv)[u];
+        inv0 = __ldg(static_cast<const A *>(p.inv) + u);
         yo0 = ld_y<T, GS>(src.y, u);
         r0 = rhs_of<A>(p, u, fin.base());
     }
     // gathers: eight slots per lane in flight
+    const uint64_t pol = policy_stream();
     for (int j0 = (ea & ~3) + 4 * lane; j0 < eb; j0 += 256) {
         const int j1 = j0 + 128;
-        const int4 q0 = __ldg(reinterpret_cast<const int4 *>(p.row_idx + j0));
-        const int4 q1 = j1 < eb ? __ldg(reinterpret_cast<const int4 *>(p.row_idx + j1))
-                                : make_int4(0, 0, 0, 0);
+        const int4 q0 = ld_idx4(p.row_idx + j0, pol);
+        const int4 q1 = j1 < eb ? ld_idx4(p.row_idx + j1, pol) : make_int4(0, 0, 0, 0);
         const int v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
         A got[8];
 #pragma unroll
@@ -551,7 +575,7 @@ __device__ __forceinline__ void low_item(const SweepParams &p, int k, const Src<
                 a = __ldg(p.col_ptr + u);
                 e = __ldg(p.col_ptr + u + 1);
                 od = __ldg(p.outdeg + u);
-                inv = static_cast<const A *>(p.inv)[u];
+                inv = __ldg(static_cast<const A *>(p.inv) + u);
                 yo = ld_y<T, GS>(src.y, u);
                 r = rhs_of<A>(p, u, fin.base());
             }
@@ -576,21 +600,21 @@ __device__ __forceinline__ void low_item(const SweepParams &p, int k, const Src<
     }
 }
 
-// mid item j (a group of vertices of one sub-range)
+// mid item j (vertices [d.x, d.y) of one sub-range)
 template <typename T, typename A, bool GS, bool W, typename Fin>
-__device__ __forceinline__ void mid_item(const SweepParams &p, int j, const Src<T, GS> &src,
-                                         Fin &fin, int lane)
+__device__ __forceinline__ void mid_item(const SweepParams &p, int j, const int4 &d,
+                                         const Src<T, GS> &src, Fin &fin, int lane)
 {
-    if (j < p.mi[1]) mid_group<32, T, A, GS, W>(p, p.mb[0] + j, p.mb[1], src, fin, lane);
-    else if (j < p.mi[2]) mid_group<16, T, A, GS, W>(p, p.mb[1] + 2 * (j - p.mi[1]), p.mb[2], src, fin, lane);
-    else if (j < p.mi[3]) mid_group<8, T, A, GS, W>(p, p.mb[2] + 4 * (j - p.mi[2]), p.mb[3], src, fin, lane);
-    else mid_group<4, T, A, GS, W>(p, p.mb[3] + 8 * (j - p.mi[3]), p.mb[4], src, fin, lane);
+    if (j < p.mi[1]) mid_group<32, T, A, GS, W>(p, d.x, d.y, src, fin, lane);
+    else if (j < p.mi[2]) mid_group<16, T, A, GS, W>(p, d.x, d.y, src, fin, lane);
+    else if (j < p.mi[3]) mid_group<8, T, A, GS, W>(p, d.x, d.y, src, fin, lane);
+    else mid_group<4, T, A, GS, W>(p, d.x, d.y, src, fin, lane);
 }
 
-// The persistent sweep body: staging, then this warp's items of the kinds of
-// this launch (hub segments, then mid groups, then low tiles), taken
-// round-robin by global warp index.  If a bounded wait gives up, the error
-// is recorded in the state and the block skips its items.
+// The persistent sweep body: staging, then this warp's share of the launch's
+// items [item_lo, item_hi) (in item order: hub segments, mid groups, low
+// tiles), taken round-robin by global warp index.  If a bounded wait gives
+// up, the error is recorded in the state and the block skips its items.
 template <typename T, typename A, bool GS, bool W, typename Fin>
 __device__ __forceinline__ void run_items(const SweepParams &p, const T *yin, Fin &fin)
 {
@@ -623,24 +647,33 @@ __device__ __forceinline__ void run_items(const SweepParams &p, const T *yin, Fi
     unsigned char *slice = dyn_smem + L.warps + warp * L.wbytes;
     const int gw = blockIdx.x * SWEEP_WARPS + warp;
     const int nw = gridDim.x * SWEEP_WARPS;
-    const int nh = (p.kinds & KIND_HUB) ? p.nhubseg : 0;
-    const int nm = (p.kinds & KIND_MID) ? p.mi[4] : 0;
-    const int nl = (p.kinds & KIND_LOW) ? p.nlt : 0;
+    const int nh = p.nhubseg, nm = p.mi[4];
+    const int first = p.item_lo;
+    const int total = p.item_hi - p.item_lo;
     // round r gives warp gw item r*nw + gw (r even) or r*nw + nw-1-gw (r odd):
     // the items' cost falls within each class, and alternating the direction
     // keeps any warp from always taking the dearest item of a round
-    const int total = nh + nm + nl;
+    auto item_at = [&](int r) { return r * nw + ((r & 1) ? nw - 1 - gw : gw); };
+    // descriptors are loaded two items ahead
+    const int4 none = make_int4(0, 0, 0, 0);
+    int4 dcur = item_at(0) < total ? __ldg(p.desc + first + item_at(0)) : none;
+    int4 dnext = item_at(1) < total ? __ldg(p.desc + first + item_at(1)) : none;
     for (int r = 0;; ++r) {
-        const int i = r * nw + ((r & 1) ? nw - 1 - gw : gw);
+        const int i = item_at(r);
         if (i >= total) break;
-        if (i < nh) hub_item<T, A, GS, W>(p, i, src, fin, lane);
-        else if (i < nh + nm) mid_item<T, A, GS, W>(p, i - nh, src, fin, lane);
-        else low_item<T, A, GS, W>(p, i - nh - nm, src, fin, lane, slice, L);
+        const int i2 = item_at(r + 2);
+        const int4 dnext2 = i2 < total ? __ldg(p.desc + first + i2) : none;
+        const int k = first + i;
+        if (k < nh) hub_item<T, A, GS, W>(p, k, dcur, src, fin, lane);
+        else if (k < nh + nm) mid_item<T, A, GS, W>(p, k - nh, dcur, src, fin, lane);
+        else low_item<T, A, GS, W>(p, dcur, src, fin, lane, slice, L);
+        dcur = dnext;
+        dnext = dnext2;
     }
 }
 
 template <typename T, typename A, bool GS, bool W>
-__global__ void __launch_bounds__(SWEEP_BS, 1) k_sweep(SweepParams p)
+__global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_sweep(SweepParams p)
 {
     SolveState *st = p.st;
     if (st->done) {

@@ -124,17 +124,24 @@ def test_batched_rejects_bad_seed(s12):
 
 
 def test_batched_full_size_s20_sampled():
-    """R-MAT scale 20 with 256 one-hot teleports at the 1e-8 stop: sampled
-    columns against the oracle's single-teleport fixed point."""
+    """R-MAT scale 20 with 256 one-hot teleports at the 1e-8 stop (iterates of
+    1 GB, beyond L2): sampled FP32 columns against the oracle's single-teleport
+    fixed point, sampled FP64 columns against the oracle's Jacobi with the
+    same stop."""
     n, src, dst = gen.rmat(20, 16, seed=4)
     og = oracle.build_graph(n, src, dst)
     g = graph(n, src, dst)
     seeds = gen.seed_vertices(256, n, seed=1)
     X, res = g.solve_batched(dev(seeds), threshold=TAU)
     assert sum(r.status == 0 for r in res) >= 0.9 * 256
+    X64, r64 = g.solve_batched(dev(seeds), threshold=TAU, precision="fp64")
+    assert all(r.status == 0 for r in r64)
     for b in (0, 131, 255):
         tele = np.zeros(n)
         tele[seeds[b]] = 1.0
         star = oracle.fixed_point(og, D, tele=tele, dangling_along_tele=True, max_iter=400)
         assert l1(X[:, b].cpu().numpy(), star.x) <= FP32_BOUND, b
+        run = oracle.jacobi(og, D, tau=TAU, max_iter=1000, tele=tele, dangling_along_tele=True)
+        assert abs(r64[b].iters - run.iters) <= 1
+        assert l1(X64[:, b].cpu().numpy(), run.x) <= 1e-12, b
     g.close()

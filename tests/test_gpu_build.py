@@ -11,7 +11,7 @@ from gpu_util import graph
 pytestmark = pytest.mark.gpu
 
 
-def check_build(n, src, dst, t_lo=16, t_hub=1024):
+def check_build(n, src, dst, t_lo=32, t_hub=4096):
     g = graph(n, src, dst)
     ex = g.export(csr=True)
     o = oracle.build_graph(n, src, dst)
