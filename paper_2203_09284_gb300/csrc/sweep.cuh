@@ -428,10 +428,17 @@ __device__ __forceinline__ A group_stream(const SweepParams &p, const Src<T, GS>
     A acc = 0;
     const A *ew = static_cast<const A *>(p.ew);
     const uint64_t pol = policy_stream();
-    for (int j0 = (a & ~3) + 4 * gl; j0 < e; j0 += 8 * G) {
+    // the next step's indices are loaded while this step's gathers are in
+    // flight, so a long in-list costs one round trip per step, not two
+    const int4 zero = make_int4(0, 0, 0, 0);
+    int j0 = (a & ~3) + 4 * gl;
+    int4 q0 = j0 < e ? ld_idx4(p.row_idx + j0, pol) : zero;
+    int4 q1 = j0 + 4 * G < e ? ld_idx4(p.row_idx + j0 + 4 * G, pol) : zero;
+    for (; j0 < e; j0 += 8 * G) {
         const int j1 = j0 + 4 * G;
-        const int4 q0 = ld_idx4(p.row_idx + j0, pol);
-        const int4 q1 = j1 < e ? ld_idx4(p.row_idx + j1, pol) : make_int4(0, 0, 0, 0);
+        const int n0 = j0 + 8 * G, n1 = n0 + 4 * G;
+        const int4 r0 = n0 < e ? ld_idx4(p.row_idx + n0, pol) : zero;
+        const int4 r1 = n1 < e ? ld_idx4(p.row_idx + n1, pol) : zero;
         const int v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
         A got[8];
 #pragma unroll
@@ -445,6 +452,8 @@ __device__ __forceinline__ A group_stream(const SweepParams &p, const Src<T, GS>
             if constexpr (W) got[c] = (s >= a && s < e) ? ew[s] * got[c] : A(0);
             acc += got[c];
         }
+        q0 = r0;
+        q1 = r1;
     }
     return acc;
 }
