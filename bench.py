@@ -416,14 +416,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the batched, multi-graph and adjoint measurements")
-    ap.add_argument("--mode", default="bench", choices=["bench", "sweeps"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "sweeps", "thresholds"],
                     help="sweeps: only build the workload graph and run --sweeps plain "
-                         "sweeps as separate launches (for profiler captures)")
+                         "sweeps as separate launches (for profiler captures); "
+                         "thresholds: sweeps and L1 error to x* of the Jacobi and fused "
+                         "FP64 solves over stop thresholds 1e-6 .. 1e-15")
     ap.add_argument("--sweeps", type=int, default=4)
     ap.add_argument("--variant", default="jacobi", choices=["jacobi", "gs"])
     args = ap.parse_args()
     if args.mode == "sweeps":
         run_sweeps(args)
+        return
+    if args.mode == "thresholds":
+        run_thresholds(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -467,6 +472,38 @@ def run_sweeps(args):
                       "outer": r.outer_iters, "precision": args.precision,
                       "variant": args.variant}))
     g.close()
+
+
+def run_thresholds(args):
+    """Sweeps to stop and L1 distance to the fixed point x* for Jacobi and the
+    fused sweep (FP64) over stop thresholds, on R-MAT graphs of scale 21-23
+    with edge factor 20 (the paper's synthetic rows).  x* is the GPU's FP64
+    Jacobi iterate run to round-off stagnation (L1 change at 1e-16 level),
+    within d/(1-d) times its last change of the true fixed point."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2203_09284_gb300 as fp
+    dev = torch.device("cuda", 0)
+    taus = [10.0 ** -k for k in range(6, 16)]
+    for scale in (21, 22, 23):
+        n, s_h, d_h = gen.rmat(scale, 20, seed=1)
+        g = fp.Graph(n, torch.from_numpy(s_h).to(dev), torch.from_numpy(d_h).to(dev))
+        hist = torch.zeros(400, dtype=torch.float64, device=dev)
+        xs, rs = g.solve(threshold=0.0, max_iter=400, history=hist)
+        star = xs.clone()
+        rows = []
+        for tau in taus:
+            row = {"tau": tau}
+            for v in ("jacobi", "gs"):
+                x, r = g.solve(variant=v, threshold=tau, max_iter=2000)
+                row[v] = {"sweeps": r.iters, "l1_to_xstar": float((x - star).abs().sum())}
+            rows.append(row)
+        print(json.dumps({"mode": "thresholds", "workload": f"rmat{scale}_ef20_seed1", "n": n,
+                          "edges": len(s_h),
+                          "xstar_last_change": float(hist[rs.iters - 1]), "rows": rows}))
+        g.close()
 
 
 def reference_arm(args):
