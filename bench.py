@@ -318,11 +318,25 @@ def run_ours(args, rank, world):
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
     achieved = alg / (sweep_ms * 1e-3) / 1e9
+    # the gathers alone (same index stream, same staging of the first 64 KB):
+    # a measured ceiling for the irregular part of the sweep
+    ex = g.export()
+    idx = ex["rrow_idx"]
+    del ex
+    yv = torch.rand(n, dtype=torch.float32, device=dev)
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    hot = min(n, 16384)
+    probe_ms, _ = timed(lambda: fp.pr_gather_probe(idx, yv, sink, hot=hot, stream=stream), 5)
+    del idx, yv
+    gather_probe = {"gathers_per_s_G": round(m / (probe_ms * 1e-3) / 1e9, 1),
+                    "probe_us": round(probe_ms * 1e3, 2),
+                    "sweep_gather_rate_frac": round(probe_ms / sweep_ms, 3)}
     traffic = args.traffic if args.traffic is not None else sweep_traffic()
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": f"k_sweep<{sweep_prec}, jacobi>", "sweep_us": round(sweep_ms * 1e3, 2),
-                "alg_bytes_per_sweep": alg, "peak_source": peak_src}
+                "alg_bytes_per_sweep": alg, "peak_source": peak_src,
+                "gather_probe": gather_probe}
 
     # ---- end to end through the public API with host buffers --------------
     src_pin = torch.from_numpy(src_h).pin_memory()

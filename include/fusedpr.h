@@ -181,8 +181,9 @@ pr_status pr_graph_info(const pr_graph *g, int32_t *n, int64_t *m, int32_t *n_da
  * bit-exact checks: outdeg/indeg [n], col_ptr/row_ptr [n+1], row_idx/csc_eid
  * [m] (in-lists), col_idx/csr_eid [m] (out-lists, ordered by (dst, input
  * position); built on demand), inv_outdeg [n] (FP64); the degree-ordered
- * numbering: new_to_old [n], rcol_ptr [n+1], rrow_idx [m] (in-lists in the
- * new ids, sources ascending, ties by input position).
+ * numbering: new_to_old [n], rcol_ptr [n+1], rrow_idx [m] (the in-list of
+ * new vertex k is the input-id in-list of new_to_old[k], in the same order,
+ * with its sources renamed to new ids).
  */
 pr_status pr_graph_export(pr_graph *g, int32_t *outdeg, int32_t *indeg, int32_t *col_ptr,
                           int32_t *row_idx, int32_t *csc_eid, int32_t *row_ptr,
@@ -267,6 +268,21 @@ pr_status pr_backward(pr_graph *g, const pr_options *o, const double *x, const d
  */
 pr_status pr_scan_exclusive_noalloc(const int32_t *in, int32_t *out, int64_t count,
                                     void *stream);
+
+/*
+ * Diagnostic (no counterpart in the paper, computes nothing of the method):
+ * *sink += sum over j < m of y[idx[j]], with the sweep's access pattern
+ * (16-byte index loads kept out of L1, eight gathers in flight per lane, the
+ * first `hot` entries of y read from shared memory, one 1024-thread block
+ * per SM).  Timed by the caller, it gives the rate at which this device
+ * serves the sweep's irregular gathers alone.
+ *   idx   device int32 [m], 16-byte aligned, every entry in [0, n)
+ *   y     device float [n];  hot: 0 <= hot <= min(n, 49152)
+ *   sink  device float [1], accumulated with atomics
+ * Returns without synchronising.
+ */
+pr_status pr_gather_probe(const int32_t *idx, int64_t m, const float *y, int32_t n, int32_t hot,
+                          float *sink, void *stream);
 
 /* Static string for a status code. */
 const char *pr_status_string(pr_status s);

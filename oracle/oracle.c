@@ -158,9 +158,10 @@ int orc_relabel(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
             ndst[e] = o2n[dst[e]];
             eids[e] = (int32_t)e;
         }
-        /* in-lists by (new dst, new src, edge id): sort by new src, then
-         * stably by new dst */
-        rc = counting_sort(m, n, nsrc, eids, tmp, NULL);
+        /* in-lists by (new dst, input src, edge id): each new in-list is
+         * the input-id in-list of the same vertex, in the same order, with
+         * its sources renamed: sort by input src, then stably by new dst */
+        rc = counting_sort(m, n, src, eids, tmp, NULL);
     }
     if (rc == ORC_OK) rc = counting_sort(m, n, ndst, tmp, rcsc_eid, rcol_ptr);
     if (rc == ORC_OK)

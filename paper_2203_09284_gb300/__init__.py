@@ -24,7 +24,7 @@ __all__ = [
     "PrOptions", "PrResult", "PrTune", "PrAllocator", "PageRankError", "lib", "library_path",
     "pr_options_default", "pr_graph_create", "pr_graph_destroy", "pr_graph_info",
     "pr_graph_export", "pr_solve", "pr_solve_batched", "pr_solve_multi", "pr_backward",
-    "pr_scan_exclusive_noalloc", "pr_status_string", "pr_last_error", "pr_kernel_launches", "Graph",
+    "pr_scan_exclusive_noalloc", "pr_gather_probe", "pr_status_string", "pr_last_error", "pr_kernel_launches", "Graph",
 ]
 
 PR_OK, PR_ERR_INVALID_ARG, PR_ERR_OOM, PR_ERR_CUDA = 0, 1, 2, 3
@@ -119,6 +119,7 @@ def lib():
             L.pr_backward.argtypes = [vp, ctypes.POINTER(PrOptions), vp, vp, vp, vp,
                                       ctypes.POINTER(PrResult), vp]
             L.pr_scan_exclusive_noalloc.argtypes = [vp, vp, i64, vp]
+            L.pr_gather_probe.argtypes = [vp, i64, vp, i32, i32, vp, vp]
             L.pr_status_string.argtypes = [ctypes.c_int]
             L.pr_status_string.restype = ctypes.c_char_p
             L.pr_last_error.argtypes = []
@@ -127,7 +128,7 @@ def lib():
             L.pr_kernel_launches.restype = ctypes.c_uint64
             for name in ("pr_options_default", "pr_graph_create", "pr_graph_info",
                          "pr_graph_export", "pr_solve", "pr_solve_batched", "pr_solve_multi",
-                         "pr_backward", "pr_scan_exclusive_noalloc"):
+                         "pr_backward", "pr_scan_exclusive_noalloc", "pr_gather_probe"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -307,6 +308,13 @@ def pr_scan_exclusive_noalloc(inp, out, count=None, stream=None):
     count = int(inp.numel()) if count is None else int(count)
     st = lib().pr_scan_exclusive_noalloc(_ptr(inp), _ptr(out), count, _stream(stream))
     _check(st, "pr_scan_exclusive_noalloc")
+
+
+def pr_gather_probe(idx, y, sink, hot=0, stream=None):
+    """sink += sum of y[idx] with the sweep's gather pattern (diagnostic)."""
+    st = lib().pr_gather_probe(_ptr(idx), int(idx.numel()), _ptr(y), int(y.numel()), int(hot),
+                               _ptr(sink), _stream(stream))
+    _check(st, "pr_gather_probe")
 
 
 def pr_backward(handle, options, x, grad_x, grad_w=None, grad_d=None, stream=None):

@@ -7,7 +7,7 @@
 //   2. in-lists in the input ids: stable radix sort of (dst, src) keys
 //   3. 1/outdeg, dangling count, largest in-degree          (k_vertex_init)
 //   4. degree-ordered ids: stable radix sort of vertices by in-degree,
-//      largest first; in-lists re-sorted in the new ids
+//      largest first; each in-list copied with its sources renamed
 //   5. work items: hub segments over [0, nhub), mid sub-ranges, low tiles
 //   6. (on demand) out-lists; (weighted graphs) row sums and P per slot
 #include <string.h>
@@ -74,14 +74,26 @@ __global__ void k_relabel_vertex(int32_t n, const int32_t *__restrict__ n2o,
     r_inv32[k] = od > 0 ? 1.0f / (float)od : 0.0f;
 }
 
-__global__ void k_make_rcsc_keys(int64_t m, const int32_t *__restrict__ src,
-                                 const int32_t *__restrict__ dst, const int32_t *__restrict__ o2n,
-                                 uint64_t *keys, int32_t *vals)
+// The in-list of new vertex k is the input-id in-list of n2o[k], in the same
+// order, with its sources renamed (warp per vertex, coalesced copies).
+__global__ void k_relabel_lists(int32_t n, const int32_t *__restrict__ n2o,
+                                const int32_t *__restrict__ o2n,
+                                const int32_t *__restrict__ col_ptr,
+                                const int32_t *__restrict__ row_idx,
+                                const int32_t *__restrict__ csc_eid,
+                                const int32_t *__restrict__ r_col_ptr, int32_t *r_row_idx,
+                                int32_t *r_csc_eid)
 {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m) return;
-    keys[e] = ((uint64_t)(uint32_t)o2n[dst[e]] << 32) | (uint64_t)(uint32_t)o2n[src[e]];
-    vals[e] = (int32_t)e;
+    const int lane = threadIdx.x & 31;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n;
+         k += (gridDim.x * blockDim.x) >> 5) {
+        const int u = n2o[k];
+        const int a = col_ptr[u], len = col_ptr[u + 1] - a, b = r_col_ptr[k];
+        for (int i = lane; i < len; i += 32) {
+            r_row_idx[b + i] = o2n[row_idx[a + i]];
+            r_csc_eid[b + i] = csc_eid[a + i];
+        }
+    }
 }
 
 // -------------------------------------------------------------- work items
@@ -527,17 +539,11 @@ static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, 
         st = scan_exclusive(g, r_indeg.as<int32_t>(), g->r_col_ptr.as<int32_t>(), n, s);
     }
     if (st == PR_OK && m > 0) {
-        k_make_rcsc_keys<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
-            m, src, dst, g->o2n.as<int32_t>(), k1.as<uint64_t>(), g->r_csc_eid.as<int32_t>());
+        k_relabel_lists<<<g->num_sms * 16, 256, 0, s>>>(
+            n, g->n2o.as<int32_t>(), g->o2n.as<int32_t>(), g->col_ptr.as<int32_t>(),
+            g->row_idx.as<int32_t>(), g->csc_eid.as<int32_t>(), g->r_col_ptr.as<int32_t>(),
+            g->r_row_idx.as<int32_t>(), g->r_csc_eid.as<int32_t>());
         note_launch();
-        std::vector<int> shifts = digit_shifts(n, 0);
-        for (int sh : digit_shifts(n, 32)) shifts.push_back(sh);
-        st = sort_pairs(g, k1.as<uint64_t>(), g->r_csc_eid.as<int32_t>(), m, shifts, s);
-        if (st == PR_OK) {
-            k_split_keys<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, k1.as<uint64_t>(),
-                                                                     g->r_row_idx.as<int32_t>());
-            note_launch();
-        }
     }
     drop_temp(g, k1, s);
     drop_temp(g, r_indeg, s);

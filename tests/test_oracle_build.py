@@ -111,7 +111,7 @@ def test_relabel_matches_numpy(case):
     o2n = np.empty(n, np.int64)
     o2n[want] = np.arange(n)
     ns, nd = o2n[src], o2n[dst]
-    order = np.lexsort((np.arange(len(src)), ns, nd))
+    order = np.lexsort((np.arange(len(src)), src, nd))  # new dst, input src, edge id
     assert np.array_equal(reid, order)
     assert np.array_equal(rrow, ns[order])
     assert np.array_equal(rcol, np.concatenate([[0], np.cumsum(np.bincount(nd, minlength=n))]))
