@@ -139,6 +139,22 @@ def b_alg(n, m, prec):
     return 4 * m + 4 * (n + 1) + 3 * s * n
 
 
+def max_over_ranks(value, world, device=None):
+    """The largest of the ranks' values (the job's time is its slowest
+    rank's); the value itself when there is one rank."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_backend():
+    import torch
+    return "nccl" if torch.cuda.is_available() else "gloo"
+
+
 def measure_rows(dev, stream, peak, timed):
     """The other rows of the hot path, each timed with CUDA events on its
     stream (outside the headline step): batched personalised PageRank at
@@ -271,10 +287,7 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     ms_total = ev0.elapsed_time(ev1)
     launches = fp.kernel_launches() - launches0
-    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_step = float(t.item()) / args.steps
+    ms_step = max_over_ranks(ms_total, world, dev) / args.steps
     sweeps = sum(r.iters + r.outer_iters for r in all_res[-1])
     value = world * m * sweeps / (ms_step * 1e-3) / 1e9
 
@@ -449,11 +462,11 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
         import torch
-        torch.distributed.init_process_group("nccl")
+        torch.distributed.init_process_group(dist_backend())
 
     if args.impl == "reference":
         if rank == 0:
-            line = reference_arm(args)
+            line = reference_arm(args, world)
             print(json.dumps(line))
         if world > 1:
             import torch
@@ -520,8 +533,9 @@ def run_thresholds(args):
         g.close()
 
 
-def reference_arm(args):
-    """The oracle timed as it stands, on the host cores, on bounded samples."""
+def reference_arm(args, world=1):
+    """The oracle timed as it stands, on the host cores, on bounded samples
+    (rank 0 only; under torchrun the other ranks do no work)."""
     import oracle
     n, src, dst = workload(args.scale)
     m = len(src)
@@ -538,7 +552,7 @@ def reference_arm(args):
     sample = (f"{2 * per_step} FP64 sweeps ({per_step} Jacobi + {per_step} fused) of the "
               f"R-MAT-{args.scale} graph per step, single thread")
     return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GTEPS",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt * 1e3, 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"rmat{args.scale}_ef16_dangling10_seed1", "n": n,
