@@ -214,3 +214,36 @@ def test_full_size_rmat22_properties():
         assert res <= limit, (v, prec, res)
         assert abs(xs.sum() - 1) < 1e-12 and (xs >= (1 - D) / n * (1 - 1e-9)).all()
     g.close()
+
+
+@pytest.mark.parametrize("variant", ["jacobi", "gs"])
+def test_defect_correction_start_vector_and_linf(s16, variant):
+    """Defect correction from a random start vector and with the max-norm
+    stop rule (Eq. 3): the FP64 residual meets the threshold."""
+    n, src, dst, og, g, star = s16
+    x0 = torch.from_numpy(gen.random_x0(n, 9)).cuda()
+    x, r = g.solve(variant=variant, precision="fp32_dc", threshold=1e-10, x0=x0)
+    assert r.status == 0 and l1(x, star.x) <= DC_BOUND
+    x, r = g.solve(variant=variant, precision="fp32_dc", threshold=1e-13, norm="linf")
+    assert r.status == 0 and r.residual <= 1e-13
+    xs = x.cpu().numpy()
+    fx = oracle.jacobi(og, D, tau=-1, max_iter=1, x0=xs, normalize=False).x
+    assert np.abs(fx - xs).max() <= 1.0001e-13
+
+
+def test_tiny_and_degenerate_graphs():
+    """n = 1 with a self-loop, a 2-cycle with a dangling tail, and two
+    disconnected components: every variant and precision agrees with the
+    dense solve of the Google matrix."""
+    cases = [(1, [0], [0]), (3, [0, 1, 1], [1, 0, 2]), (6, [0, 1, 2, 3, 4], [1, 2, 0, 4, 3])]
+    for n, s, t in cases:
+        s = np.array(s, np.int32)
+        t = np.array(t, np.int32)
+        want = oracle.dense_pagerank(n, s, t, D)
+        g = graph(n, s, t)
+        for v in ("jacobi", "gs"):
+            for prec in ("fp64", "fp32_dc"):
+                x, r = g.solve(variant=v, precision=prec, threshold=1e-13, max_iter=2000)
+                assert r.status == 0, (n, v, prec)
+                assert np.abs(x.cpu().numpy() - want).max() < 1e-12, (n, v, prec)
+        g.close()
