@@ -144,6 +144,8 @@ __global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_dc_resid(DCParams q)
         sx->scale = scale;
         se->iter = 0;
         se->done = 0;
+        se->best = INFINITY;
+        se->since = 0;
         se->dang = dang_r / scale;
         se->sum = sum_r / scale;
         se->sigma = scale;
@@ -212,13 +214,16 @@ __global__ void k_dc_first_e(DCParams q)
     }
 }
 
-static double default_eta(pr_precision pr)
+// Inner stop, relative to ||r||_1 (measured at R-MAT scale 22: the FP32 forms
+// reach the FP64 threshold in the fewest sweeps with these; the 16-bit
+// forms stop near their storage precision).
+static double default_eta(pr_precision pr, bool gs)
 {
     switch (pr) {
-    case PR_FP32_DC: return 1e-6;
+    case PR_FP32_DC: return gs ? 3e-5 : 1e-5;
     case PR_FP16_DC: return 4e-3;
     case PR_BF16_DC: return 3e-2;
-    default: return 1e-6;
+    default: return 1e-5;
     }
 }
 
@@ -383,7 +388,7 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     SolveState *hs = g->host_state;
     init_state(g, o, hs[0]);
     hs[0].max_outer = o->max_outer > 0 ? o->max_outer : default_max_outer(o->precision);
-    hs[0].inner_rel = o->inner_rel > 0 ? o->inner_rel : default_eta(o->precision);
+    hs[0].inner_rel = o->inner_rel > 0 ? o->inner_rel : default_eta(o->precision, gs);
     hs[0].scale = 1.0;
     memset(&hs[1], 0, sizeof(SolveState));
     hs[1].d = o->d;

@@ -354,7 +354,16 @@ __device__ __forceinline__ void close_sweep(const SweepParams &p)
         st->inner_iter += 1;
         if (so->history) so->history[total - 1] = err;
         conv = err <= st->tau;
-        stop = conv || it >= st->max_iter || total >= so->max_iter || error;
+        // an inner solve whose change stops falling has reached the
+        // correction's storage precision: hand over to the FP64 step
+        if (err < st->best) {
+            st->best = err;
+            st->since = 0;
+        } else {
+            st->since += 1;
+        }
+        const bool stalled = st->since >= 8;
+        stop = conv || stalled || it >= st->max_iter || total >= so->max_iter || error;
         if (p.shift) {
             // e <- e + beta x with sum(e) = mass_target afterwards; in stored
             // units e~ += gamma Y64 (the shift kernel applies it), so the

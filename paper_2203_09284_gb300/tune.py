@@ -20,17 +20,18 @@ DEFAULT_CANDIDATES = [
 
 
 def graph_signature(info: dict, device_name: str, precision: str, variant: str) -> str:
-    """Cache key: device, sweep kind and the graph's size and degree classes
-    rounded to two significant digits (graphs of one family share it)."""
+    """Cache key: device, sweep kind and the graph's vertex, edge and dangling
+    counts rounded to two significant digits (graphs of one family share
+    it; the class sizes are left out: they follow the last launch
+    parameters used)."""
     def r2(v):
         v = int(v)
         if v < 100:
             return v
         s = len(str(v)) - 2
         return round(v, -s)
-    low, mid, hub = info["bins"]
     return "|".join(str(x) for x in (device_name, precision, variant, r2(info["n"]),
-                                      r2(info["m"]), r2(info["n_dangling"]), r2(mid), r2(hub)))
+                                      r2(info["m"]), r2(info["n_dangling"])))
 
 
 def sweep_time_ms(solve, sweeps: int = 8, reps: int = 2) -> float:

@@ -19,10 +19,16 @@ def test_default_candidates_are_distinct_and_complete():
                for c in tune.DEFAULT_CANDIDATES)
 
 
+def sa_eq(x, y):
+    return (tune.graph_signature(x, "GB300", "fp32", "jacobi")
+            == tune.graph_signature(y, "GB300", "fp32", "jacobi"))
+
+
 def test_signature_groups_graphs_of_one_family():
     a = {"n": 4194304, "m": 67008246, "n_dangling": 419430, "bins": [3914232, 278278, 1794]}
     b = {"n": 4194304, "m": 67011000, "n_dangling": 419431, "bins": [3914000, 278100, 1790]}
     c = dict(a, m=33000000)
+    assert sa_eq(a, dict(a, bins=[1, 2, 3]))
     sa = tune.graph_signature(a, "GB300", "fp32", "jacobi")
     assert sa == tune.graph_signature(b, "GB300", "fp32", "jacobi")
     assert sa != tune.graph_signature(c, "GB300", "fp32", "jacobi")
