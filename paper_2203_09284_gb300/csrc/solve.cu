@@ -82,10 +82,7 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs)
     p.hubseg_start = it.hubseg_start.as<int32_t>();
     p.seg_acc = it.seg_acc.as<double>();
     p.hub_cnt = it.hub_cnt.as<int32_t>();
-    for (int k = 0; k < 5; ++k) {
-        p.mb[k] = it.mb[k];
-        p.mi[k] = it.mi[k];
-    }
+    for (int k = 0; k < 5; ++k) p.mi[k] = it.mi[k];
     p.nlt = it.nlt;
     p.lcap = it.lcap;
     // staged copy of stage_kb KB, at most the room left beside the warp

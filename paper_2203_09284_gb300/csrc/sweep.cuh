@@ -84,9 +84,8 @@ struct SweepParams {
     const int32_t *hubseg_start;  // [nhub + 1]
     double *seg_acc;              // [nhubseg]
     int32_t *hub_cnt;             // [nhub]
-    int32_t mb[5];                // mid sub-range k = [mb[k], mb[k+1]): 32 >> k
-                                  // lanes per vertex
-    int32_t mi[5];                // items before sub-range k (mi[4]: all mid items)
+    int32_t mi[5];                // mid items before sub-range k (32 >> k lanes
+                                  // per vertex; mi[4]: all mid items)
     int32_t nlt;
     int32_t lcap;                 // per-warp slots for a low tile's in-edges
     int32_t stage;                // y[0, stage) is copied to shared memory
