@@ -47,8 +47,9 @@
 // updated in this sweep).  The hottest vertices (hubs and the mid vertices
 // with more than 128 in-edges) are updated by a first launch, so the second
 // launch's shared-memory copy and loads already see their new values; inside
-// a low tile, a vertex reads the new values of the tile's earlier vertices.  After each fused sweep the
-// iterate is rescaled to sum 1 by folding 1/sum into sigma.
+// a low tile, a vertex reads the new values of the tile's earlier vertices.
+// After each fused sweep the iterate is rescaled to sum 1 by folding 1/sum
+// into sigma.
 #pragma once
 
 #include "common.cuh"
@@ -56,14 +57,10 @@
 
 namespace fpr {
 
-#ifndef SWEEP_THREADS
-#define SWEEP_THREADS 1024
-#endif
-#ifndef SWEEP_BLOCKS_PER_SM
-#define SWEEP_BLOCKS_PER_SM 1
-#endif
-constexpr int SWEEP_BS = SWEEP_THREADS;          // threads per sweep block
-constexpr int SWEEP_MINB = SWEEP_BLOCKS_PER_SM;  // resident sweep blocks per SM
+// One 1024-thread block per SM: 64 registers a thread fill the register file
+// (smaller blocks at 2-6 per SM with fewer registers measured slower).
+constexpr int SWEEP_BS = 1024;  // threads per sweep block
+constexpr int SWEEP_MINB = 1;   // resident sweep blocks per SM
 constexpr int SWEEP_WARPS = SWEEP_BS / 32;
 constexpr uint32_t DEFAULT_WAIT_LIMIT = 1u << 22;
 
