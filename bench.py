@@ -447,11 +447,13 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the batched, multi-graph and adjoint measurements")
-    ap.add_argument("--mode", default="bench", choices=["bench", "sweeps", "thresholds"],
+    ap.add_argument("--mode", default="bench",
+                    choices=["bench", "sweeps", "thresholds", "linf"],
                     help="sweeps: only build the workload graph and run --sweeps plain "
                          "sweeps as separate launches (for profiler captures); "
                          "thresholds: sweeps and L1 error to x* of the Jacobi and fused "
-                         "FP64 solves over stop thresholds 1e-6 .. 1e-15")
+                         "FP64 solves over stop thresholds 1e-6 .. 1e-15; linf: time to a "
+                         "max-norm change of 1e-15 (the paper's stop rule) for both sweeps")
     ap.add_argument("--sweeps", type=int, default=4)
     ap.add_argument("--variant", default="jacobi", choices=["jacobi", "gs"])
     args = ap.parse_args()
@@ -460,6 +462,9 @@ def main():
         return
     if args.mode == "thresholds":
         run_thresholds(args)
+        return
+    if args.mode == "linf":
+        run_linf(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -534,6 +539,41 @@ def run_thresholds(args):
         print(json.dumps({"mode": "thresholds", "workload": f"rmat{scale}_ef20_seed1", "n": n,
                           "edges": len(s_h),
                           "xstar_last_change": float(hist[rs.iters - 1]), "rows": rows}))
+        g.close()
+
+
+def run_linf(args):
+    """The paper's stop rule (max-norm change <= 1e-15, FP64): sweeps and time
+    to solution of Jacobi and the fused sweep on R-MAT graphs of scale 21-23
+    (edge factor 20) and on the benchmark's workload."""
+    import torch
+
+    import gen
+    import paper_2203_09284_gb300 as fp
+    dev = torch.device("cuda", 0)
+    cases = [(f"rmat{s}_ef20_seed1", lambda s=s: gen.rmat(s, 20, seed=1)) for s in (21, 22, 23)]
+    cases.append((f"rmat{args.scale}_ef16_dangling10_seed1", lambda: workload(args.scale)))
+    for name, make in cases:
+        n, s_h, d_h = make()
+        g = fp.Graph(n, torch.from_numpy(s_h).to(dev), torch.from_numpy(d_h).to(dev))
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        row = {"mode": "linf", "workload": name, "n": n, "edges": len(s_h), "threshold": 1e-15}
+        for v in ("jacobi", "gs"):
+            best, res = None, None
+            for _ in range(3):
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                _, r = g.solve(out=x, variant=v, threshold=1e-15, norm="linf", max_iter=5000)
+                b.record()
+                torch.cuda.synchronize()
+                t = a.elapsed_time(b)
+                if best is None or t < best:
+                    best, res = t, r
+            row[v] = {"ms": round(best, 3), "sweeps": res.iters, "status": res.status,
+                      "linf_change": res.residual}
+        row["fused_speedup"] = round(row["jacobi"]["ms"] / row["gs"]["ms"], 3)
+        print(json.dumps(row))
         g.close()
 
 

@@ -93,7 +93,7 @@ typedef struct {
     int32_t t_hub;     /* in-degree >  t_hub: hub, split into segments of
                           hub_seg in-edges, a warp per segment (default
                           4096); in between: 4 to 32 lanes per vertex */
-    int32_t hub_seg;   /* in-edges per hub segment (default 4096, 256 to
+    int32_t hub_seg;   /* in-edges per hub segment (default 2048, 256 to
                           8192) */
     int32_t tile;      /* work units (in-edges + vertices) per low-degree
                           tile, whose in-edges a warp gathers into shared

@@ -613,7 +613,7 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
     }
     g->tune.t_lo = 32;
     g->tune.t_hub = 4096;
-    g->tune.hub_seg = 4096;
+    g->tune.hub_seg = 2048;
     g->tune.tile = 256;
     g->tune.deterministic_gs = 0;
     g->tune.stage_kb = 64;
