@@ -150,7 +150,8 @@ pr_status pr_options_default(pr_options *o);
  * in-edges, ascending, ties by input position), inverse out-degrees
  * (IEEE 1.0/deg, 0 for dangling), and the sweep's working copy in a
  * degree-ordered numbering: vertices sorted by in-degree, largest first (ties
- * by id), in-lists re-sorted in the new ids.  That puts the in-degree bins in
+ * by id), each in-list kept in its input-id order with its sources renamed
+ * to the new ids.  That puts the in-degree bins in
  * contiguous ranges and packs the most-gathered contributions together.
  * Results of every solve are returned in the input ids.
  *   n       vertices, >= 1
