@@ -69,10 +69,10 @@ __global__ void k_adj_init(int32_t n, const int32_t *__restrict__ n2o, const dou
         pt.sm += gv;
     }
     block_partials<A>(st, pt);
-    if (last_block(st) && threadIdx.x == 0) {
+    if (last_block(st) && threadIdx.x < 32) {
         double res, resmax, dang, sum;
         take_sums(st, res, resmax, dang, sum);
-        st->sum = sum;
+        if (threadIdx.x == 0) st->sum = sum;
     }
 }
 
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_adj_sweep(SweepParams 
     AdjFin<T, A> fin(p, static_cast<A>(st->d), static_cast<A>(st->sum * st->inv_n), yout);
     run_items<T, A, false, true>(p, yin, fin);
     block_partials<A>(st, fin.pt);
-    if (p.close && last_block(st) && threadIdx.x == 0) close_sweep(p);
+    if (p.close && last_block(st) && threadIdx.x < 32) close_sweep(p);
 }
 
 struct GradParams {
@@ -158,10 +158,10 @@ __global__ void k_adj_grad(GradParams q, const T *__restrict__ lam)
         }
     }
     block_partials<double>(q.st, pt);
-    if (last_block(q.st) && threadIdx.x == 0) {
+    if (last_block(q.st) && threadIdx.x < 32) {
         double xpl, unused, dx, S;
         take_sums(q.st, xpl, unused, dx, S);
-        if (q.grad_d) *q.grad_d = xpl + (dx - 1.0) * S / static_cast<double>(q.n);
+        if (threadIdx.x == 0 && q.grad_d) *q.grad_d = xpl + (dx - 1.0) * S / static_cast<double>(q.n);
     }
 }
 

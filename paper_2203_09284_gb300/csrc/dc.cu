@@ -120,9 +120,10 @@ __global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_dc_resid(DCParams q)
     ResidFin<Te> fin(q, load_ctx<double>(sx));
     run_items<double, double, false, W>(q.p, q.y64, fin);
     block_partials<double>(sx, fin.pt);
-    if (!(last_block(sx) && threadIdx.x == 0)) return;
+    if (!(last_block(sx) && threadIdx.x < 32)) return;
     double res, resmax, dang_r, sum_r;
     take_sums(sx, res, resmax, dang_r, sum_r);
+    if (threadIdx.x != 0) return;
     sx->outer_iter += 1;
     const int total = sx->iter + 1;
     sx->iter = total;
@@ -187,9 +188,10 @@ __global__ void k_dc_update(DCParams q)
         if (od == 0) pt.dm += xn;
     }
     block_partials<double>(sx, pt);
-    if (!(last_block(sx) && threadIdx.x == 0)) return;
+    if (!(last_block(sx) && threadIdx.x < 32)) return;
     double res, resmax, dang, sum;
     take_sums(sx, res, resmax, dang, sum);
+    if (threadIdx.x != 0) return;
     sx->sum = sum;
     sx->dang = dang;
     sx->sigma = sum > 0 ? 1.0 / sum : 1.0;

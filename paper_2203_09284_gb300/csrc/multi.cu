@@ -55,6 +55,7 @@ __device__ __forceinline__ void multi_item(const SweepParams &p, int j, int lane
     const double lm = warp_max(static_cast<double>(fin.pt.lmax));
     const double dm = warp_sum(static_cast<double>(fin.pt.dm));
     const double sm = warp_sum(static_cast<double>(fin.pt.sm));
+    int last = 0;
     if (lane == 0) {
         AccSlot &s = st->acc[j % ACC_SLOTS];
         if (l1 != 0) fx_add(&s.res_hi, &s.res_lo, l1);
@@ -63,8 +64,9 @@ __device__ __forceinline__ void multi_item(const SweepParams &p, int j, int lane
         if (sm != 0) fx_add(&s.sum_hi, &s.sum_lo, sm);
         __threadfence();
         const unsigned nitems = (unsigned)(nh + nm + p.nlt);
-        if (atomicAdd(&st->ticket, 1u) == nitems - 1) close_sweep(p);  // resets the ticket
+        last = atomicAdd(&st->ticket, 1u) == nitems - 1;
     }
+    if (__shfl_sync(FULL, last, 0)) close_sweep(p);  // resets the ticket
     __syncwarp();
 }
 

@@ -295,39 +295,53 @@ __device__ __forceinline__ bool last_block(SolveState *st)
     return is_last;
 }
 
+// Reads and clears the sweep accumulators and the block ticket.  Called by
+// all 32 lanes of one warp: lane k takes slot k (one round trip for all
+// slots, through L2 where the atomics landed) and every lane gets the
+// totals.  The words are integers, so the tree of adds gives the same totals
+// as any other order.
 __device__ __forceinline__ void take_sums(SolveState *st, double &res, double &resmax,
                                           double &dang, double &sum)
 {
+    static_assert(ACC_SLOTS == 32, "one accumulator slot per lane");
     __threadfence();
-    long long rh = 0, rl = 0, dh = 0, dl = 0, sh = 0, sl = 0;
-    unsigned long long mx = 0;
-    for (int k = 0; k < ACC_SLOTS; ++k) {
-        volatile AccSlot *v = &st->acc[k];
-        rh += v->res_hi;
-        rl += v->res_lo;
-        dh += v->dang_hi;
-        dl += v->dang_lo;
-        sh += v->sum_hi;
-        sl += v->sum_lo;
-        mx = v->res_max > mx ? v->res_max : mx;
-        v->res_hi = v->res_lo = v->dang_hi = v->dang_lo = v->sum_hi = v->sum_lo = 0;
-        v->res_max = 0;
+    const int lane = threadIdx.x & 31;
+    longlong2 *slot = reinterpret_cast<longlong2 *>(&st->acc[lane]);
+    const longlong2 r = __ldcg(slot), dd = __ldcg(slot + 1), s = __ldcg(slot + 2),
+                    m = __ldcg(slot + 3);
+    const longlong2 zero = make_longlong2(0, 0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) __stcg(slot + k, zero);
+    long long rh = r.x, rl = r.y, dh = dd.x, dl = dd.y, sh = s.x, sl = s.y;
+    unsigned long long mx = static_cast<unsigned long long>(m.x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rh += __shfl_xor_sync(FULL, rh, o);
+        rl += __shfl_xor_sync(FULL, rl, o);
+        dh += __shfl_xor_sync(FULL, dh, o);
+        dl += __shfl_xor_sync(FULL, dl, o);
+        sh += __shfl_xor_sync(FULL, sh, o);
+        sl += __shfl_xor_sync(FULL, sl, o);
+        const unsigned long long m2 = __shfl_xor_sync(FULL, mx, o);
+        mx = m2 > mx ? m2 : mx;
     }
     res = fx_value(rh, rl);
     resmax = __longlong_as_double(static_cast<long long>(mx));
     dang = fx_value(dh, dl);
     sum = fx_value(sh, sl);
-    st->ticket = 0;
+    if (lane == 0) st->ticket = 0;
 }
 
 // Closes a PageRank sweep (dc == 0) or a correction sweep (dc != 0): next
 // scalars, history, stop test, loop condition.  A device-side error ends the
-// loop with that status.
+// loop with that status.  Called by all lanes of one warp (take_sums); lane
+// 0 does the rest.
 __device__ __forceinline__ void close_sweep(const SweepParams &p)
 {
     SolveState *st = p.st;
     double res, resmax, dang, sum;
     take_sums(st, res, resmax, dang, sum);
+    if (threadIdx.x & 31) return;
     const int it = st->iter + 1;
     st->iter = it;
     st->res = res;
@@ -708,7 +722,7 @@ __global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_sweep(SweepParams p)
     SweepFin<T, A, GS, W> fin(p, load_ctx<A>(st), yout);
     run_items<T, A, GS, W>(p, yin, fin);
     block_partials<A>(st, fin.pt);
-    if (p.close && last_block(st) && threadIdx.x == 0) close_sweep(p);
+    if (p.close && last_block(st) && threadIdx.x < 32) close_sweep(p);
 }
 
 // Fused sweep in strict increasing input-id order (Eq. 9 exactly): one warp,
@@ -735,7 +749,7 @@ __global__ void k_sweep_serial(SweepParams p)
         __syncwarp();
     }
     block_partials<A>(st, fin.pt);
-    if (last_block(st) && threadIdx.x == 0) close_sweep(p);
+    if (last_block(st) && threadIdx.x < 32) close_sweep(p);
 }
 
 // ------------------------------------------------------------ init/output
@@ -756,9 +770,10 @@ __global__ void k_init(int32_t n, const double *x0, const int32_t *__restrict__ 
         if (od == 0) pt.dm += x;
     }
     block_partials<A>(st, pt);
-    if (last_block(st) && threadIdx.x == 0) {
+    if (last_block(st) && threadIdx.x < 32) {
         double res, resmax, dang, sum;
         take_sums(st, res, resmax, dang, sum);
+        if (threadIdx.x != 0) return;
         st->dang = dang;
         st->sum = sum;
         st->sigma = (renorm && sum > 0) ? 1.0 / sum : 1.0;
