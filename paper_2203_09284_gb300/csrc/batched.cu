@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(BATCH_BS, 1) k_batch_sweep(BatchParams p)
     for (int k = lane; k < 2 * BP; k += 32) sh.werr[k] = 0.0;
     __syncthreads();
 
-    const int gw = blockIdx.x * BATCH_WARPS + warp, nw = gridDim.x * BATCH_WARPS;
+    // blocks interleaved: neighbouring items (like cost) go to different SMs
+    const int gw = warp * gridDim.x + blockIdx.x, nw = gridDim.x * BATCH_WARPS;
     const int nitems = p.nseg + (p.n - p.nhub);
     for (int r = 0;; ++r) {
         const int i = r * nw + ((r & 1) ? nw - 1 - gw : gw);

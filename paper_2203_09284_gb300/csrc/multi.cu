@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_multi_sweep(MultiParam
     const Layout L = make_layout(mp.lcap, sizeof(A), sizeof(T), false, 0);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned char *slice = dyn_smem + L.warps + warp * L.wbytes;
-    const int gw = blockIdx.x * SWEEP_WARPS + warp;
+    const int gw = warp * gridDim.x + blockIdx.x;  // blocks interleaved, as in run_items
     const int nw = gridDim.x * SWEEP_WARPS;
     const int total = __ldg(mp.off + mp.G);
     for (int r = 0;; ++r) {

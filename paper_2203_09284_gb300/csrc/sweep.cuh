@@ -673,7 +673,10 @@ __device__ __forceinline__ void run_items(const SweepParams &p, const T *yin, Fi
     }
     const Src<T, GS> src{yin, reinterpret_cast<const T *>(dyn_smem), p.stage};
     unsigned char *slice = dyn_smem + L.warps + warp * L.wbytes;
-    const int gw = blockIdx.x * SWEEP_WARPS + warp;
+    // global warp index, blocks interleaved: neighbouring positions of a
+    // round (items of like cost) go to different SMs, so that no SM holds a
+    // run of the dearest items
+    const int gw = warp * gridDim.x + blockIdx.x;
     const int nw = gridDim.x * SWEEP_WARPS;
     const int nh = p.nhubseg, nm = p.mi[4];
     const int first = p.item_lo;
