@@ -207,19 +207,21 @@ void release_graphs(pr_graph *g);
 pr_status scan_exclusive(pr_graph *g, const int32_t *in, int32_t *out, int64_t count,
                          cudaStream_t s);
 // stable LSD radix sort of (key, value) pairs by the 8-bit digits at `shifts`
-// (alt_k/alt_v: same-size scratch; the result ends in keys/vals)
+// (alt_k/alt_v: same-size scratch).  With kres/vres the result stays where
+// the last pass put it (keys/vals or alt_k/alt_v) and they receive it; else
+// it is copied back into keys/vals.
 pr_status radix_sort(pr_graph *g, uint64_t *keys, int32_t *vals, uint64_t *alt_k, int32_t *alt_v,
-                     int64_t m, const std::vector<int> &shifts, cudaStream_t s);
+                     int64_t m, const std::vector<int> &shifts, cudaStream_t s,
+                     uint64_t **kres = nullptr, int32_t **vres = nullptr);
 // digit shifts covering ids < n, starting at bit `offset`
 std::vector<int> digit_shifts(int32_t n, int offset);
 
 // primitives.cu kernels launched by the graph assembly
-__global__ void k_degrees(int64_t m, const int32_t *__restrict__ src,
-                          const int32_t *__restrict__ dst, int32_t n, int32_t *outdeg,
-                          int32_t *indeg, int32_t *err);
+__global__ void k_run_degrees(int64_t m, const uint64_t *__restrict__ keys, int high,
+                              int32_t *deg, int32_t *low32);
 __global__ void k_make_csc_keys(int64_t m, const int32_t *__restrict__ src,
-                                const int32_t *__restrict__ dst, uint64_t *keys, int32_t *vals);
-__global__ void k_split_keys(int64_t m, const uint64_t *__restrict__ keys, int32_t *low32);
+                                const int32_t *__restrict__ dst, int32_t n, uint64_t *keys,
+                                int32_t *vals, int32_t *err);
 __global__ void k_make_csr_keys(int32_t n, const int32_t *__restrict__ col_ptr,
                                 const int32_t *__restrict__ row_idx,
                                 const int32_t *__restrict__ csc_eid, uint64_t *keys, int32_t *vals);

@@ -3,8 +3,9 @@
 // sweep's working copy in a degree-ordered numbering.
 //
 // Build steps (all on the device, all deterministic):
-//   1. out/in-degree histograms and id validation         (k_degrees)
-//   2. in-lists in the input ids: stable radix sort of (dst, src) keys
+//   1. edge keys and id validation                         (k_make_csc_keys)
+//   2. in-lists in the input ids: stable radix sort of (dst, src) keys,
+//      out/in-degrees from the runs of the half-sorted and sorted keys
 //   3. 1/outdeg, dangling count, largest in-degree          (k_vertex_init)
 //   4. degree-ordered ids: stable radix sort of vertices by in-degree,
 //      largest first; each in-list copied with its sources renamed
@@ -75,8 +76,31 @@ __global__ void k_relabel_vertex(int32_t n, const int32_t *__restrict__ n2o,
 }
 
 // The in-list of new vertex k is the input-id in-list of n2o[k], in the same
-// order, with its sources renamed (warp per vertex, coalesced copies).
-__global__ void k_relabel_lists(int32_t n, const int32_t *__restrict__ n2o,
+// order, with its sources renamed.  The copy is flat over the output slots:
+// a warp takes a chunk of RL_SLOTS consecutive slots (coalesced writes) and
+// each lane finds the vertex of its slot by binary search of r_col_ptr
+// between the chunk's first and last owners.
+constexpr int RL_SLOTS = 1024;
+
+// owner[c]: the vertex whose in-list holds slot min(c * RL_SLOTS, m - 1)
+// (the largest k with r_col_ptr[k] <= that slot), c in [0, nchunks].
+__global__ void k_chunk_owner(int32_t n, int64_t m, int64_t nchunks,
+                              const int32_t *__restrict__ r_col_ptr, int32_t *owner)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > nchunks) return;
+    const int64_t slot = min(c * RL_SLOTS, m - 1);
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = lo + ((hi - lo + 1) >> 1);
+        if (r_col_ptr[mid] <= slot) lo = mid;
+        else hi = mid - 1;
+    }
+    owner[c] = lo;
+}
+
+__global__ void k_relabel_lists(int64_t m, int64_t nchunks, const int32_t *__restrict__ owner,
+                                const int32_t *__restrict__ n2o,
                                 const int32_t *__restrict__ o2n,
                                 const int32_t *__restrict__ col_ptr,
                                 const int32_t *__restrict__ row_idx,
@@ -85,13 +109,20 @@ __global__ void k_relabel_lists(int32_t n, const int32_t *__restrict__ n2o,
                                 int32_t *r_csc_eid)
 {
     const int lane = threadIdx.x & 31;
-    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n;
-         k += (gridDim.x * blockDim.x) >> 5) {
-        const int u = n2o[k];
-        const int a = col_ptr[u], len = col_ptr[u + 1] - a, b = r_col_ptr[k];
-        for (int i = lane; i < len; i += 32) {
-            r_row_idx[b + i] = o2n[row_idx[a + i]];
-            r_csc_eid[b + i] = csc_eid[a + i];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks; c += nw) {
+        const int ka = owner[c], kb = owner[c + 1];
+        const int64_t s1 = min(m, (c + 1) * RL_SLOTS);
+        for (int64_t j = c * RL_SLOTS + lane; j < s1; j += 32) {
+            int lo = ka, hi = kb;
+            while (lo < hi) {
+                const int mid = lo + ((hi - lo + 1) >> 1);
+                if (__ldg(r_col_ptr + mid) <= j) lo = mid;
+                else hi = mid - 1;
+            }
+            const int64_t pos = (int64_t)__ldg(col_ptr + __ldg(n2o + lo)) + (j - __ldg(r_col_ptr + lo));
+            r_row_idx[j] = o2n[row_idx[pos]];
+            r_csc_eid[j] = csc_eid[pos];
         }
     }
 }
@@ -469,16 +500,67 @@ static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, 
     PR_CUDA(cudaMemsetAsync(g->r_inv64.p, 0, sizeof(double) * ((size_t)n + 16), s));
     PR_CUDA(cudaMemsetAsync(g->r_inv32.p, 0, sizeof(float) * ((size_t)n + 16), s));
 
-    // 1. degrees (+ id and weight validation)
+    // 1. edge keys (dst << 32 | src) with their input positions, id and
+    // weight validation
+    Buf k1;
+    PR_TRY(buf_alloc(g, k1, sizeof(uint64_t) * std::max(mm, (size_t)n), s));
     if (m > 0) {
-        int blocks = (int)std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 16);
-        k_degrees<<<blocks, 256, 0, s>>>(m, src, dst, n, g->outdeg.as<int32_t>(),
-                                         g->indeg.as<int32_t>(), flags_dev);
+        k_make_csc_keys<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
+            m, src, dst, n, k1.as<uint64_t>(), g->csc_eid.as<int32_t>(), flags_dev);
         note_launch();
         if (w) {
             k_check_weights<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, w, flags_dev);
             note_launch();
         }
+    }
+    PR_LAUNCH_CHECK();
+    int32_t herr = 0;
+    PR_CUDA(cudaMemcpyAsync(&herr, flags_dev, sizeof(herr), cudaMemcpyDeviceToHost, s));
+    PR_CUDA(cudaStreamSynchronize(s));
+    if (herr & 3) {
+        drop_temp(g, k1, s);
+        if (herr & 1) set_error("pr_graph_create: an edge endpoint lies outside [0, %d)", n);
+        else set_error("pr_graph_create: edge weights must be positive and finite");
+        return PR_ERR_INVALID_ARG;
+    }
+
+    // 2. in-lists in the input ids: stable radix sort by the source digits,
+    // then by the destination digits; out-degrees are the runs of equal
+    // sources after the first half, in-degrees the runs of equal
+    // destinations at the end
+    pr_status st = PR_OK;
+    if (m > 0) {
+        Buf k2, v2;
+        st = buf_alloc(g, k2, sizeof(uint64_t) * mm, s);
+        if (st == PR_OK) st = buf_alloc(g, v2, sizeof(int32_t) * mm, s);
+        uint64_t *ka = nullptr, *kb = nullptr;
+        int32_t *va = nullptr, *vb = nullptr;
+        int32_t *eid = g->csc_eid.as<int32_t>();
+        const unsigned rb = (unsigned)std::min<int64_t>((m + 255) / 256, (int64_t)g->num_sms * 32);
+        if (st == PR_OK)
+            st = radix_sort(g, k1.as<uint64_t>(), eid, k2.as<uint64_t>(), v2.as<int32_t>(), m,
+                            digit_shifts(n, 0), s, &ka, &va);
+        if (st == PR_OK) {
+            k_run_degrees<<<rb, 256, 0, s>>>(m, ka, 0, g->outdeg.as<int32_t>(), nullptr);
+            note_launch();
+            uint64_t *kalt = ka == k1.as<uint64_t>() ? k2.as<uint64_t>() : k1.as<uint64_t>();
+            int32_t *valt = va == eid ? v2.as<int32_t>() : eid;
+            st = radix_sort(g, ka, va, kalt, valt, m, digit_shifts(n, 32), s, &kb, &vb);
+        }
+        if (st == PR_OK) {
+            k_run_degrees<<<rb, 256, 0, s>>>(m, kb, 1, g->indeg.as<int32_t>(),
+                                             g->row_idx.as<int32_t>());
+            note_launch();
+            if (vb != eid)
+                PR_CUDA(cudaMemcpyAsync(eid, vb, sizeof(int32_t) * (size_t)m,
+                                        cudaMemcpyDeviceToDevice, s));
+        }
+        drop_temp(g, k2, s);
+        drop_temp(g, v2, s);
+    }
+    if (st != PR_OK) {
+        drop_temp(g, k1, s);
+        return st;
     }
     k_vertex_init<<<(n + 255) / 256, 256, 0, s>>>(n, g->outdeg.as<int32_t>(),
                                                   g->indeg.as<int32_t>(), g->inv64.as<double>(),
@@ -487,36 +569,10 @@ static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, 
     PR_LAUNCH_CHECK();
     int32_t hflags[3] = {0, 0, 0};
     PR_CUDA(cudaMemcpyAsync(hflags, flags_dev, sizeof(hflags), cudaMemcpyDeviceToHost, s));
-    PR_CUDA(cudaStreamSynchronize(s));
-    if (hflags[0] & 1) {
-        set_error("pr_graph_create: an edge endpoint lies outside [0, %d)", n);
-        return PR_ERR_INVALID_ARG;
-    }
-    if (hflags[0] & 2) {
-        set_error("pr_graph_create: edge weights must be positive and finite");
-        return PR_ERR_INVALID_ARG;
-    }
+    st = scan_exclusive(g, g->indeg.as<int32_t>(), g->col_ptr.as<int32_t>(), n, s);
+    if (st == PR_OK) PR_CUDA(cudaStreamSynchronize(s));
     g->n_dangling = hflags[1];
     const int32_t maxd = hflags[2];
-
-    // 2. in-lists in the input ids
-    PR_TRY(scan_exclusive(g, g->indeg.as<int32_t>(), g->col_ptr.as<int32_t>(), n, s));
-    Buf k1;
-    PR_TRY(buf_alloc(g, k1, sizeof(uint64_t) * std::max(mm, (size_t)n), s));
-    pr_status st = PR_OK;
-    if (m > 0) {
-        k_make_csc_keys<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
-            m, src, dst, k1.as<uint64_t>(), g->csc_eid.as<int32_t>());
-        note_launch();
-        std::vector<int> shifts = digit_shifts(n, 0);
-        for (int sh : digit_shifts(n, 32)) shifts.push_back(sh);
-        st = sort_pairs(g, k1.as<uint64_t>(), g->csc_eid.as<int32_t>(), m, shifts, s);
-        if (st == PR_OK) {
-            k_split_keys<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(m, k1.as<uint64_t>(),
-                                                                     g->row_idx.as<int32_t>());
-            note_launch();
-        }
-    }
     // 4. degree-ordered ids
     Buf r_indeg;
     if (st == PR_OK) st = buf_alloc(g, r_indeg, sizeof(int32_t) * (size_t)n, s);
@@ -539,11 +595,22 @@ static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, 
         st = scan_exclusive(g, r_indeg.as<int32_t>(), g->r_col_ptr.as<int32_t>(), n, s);
     }
     if (st == PR_OK && m > 0) {
-        k_relabel_lists<<<g->num_sms * 16, 256, 0, s>>>(
-            n, g->n2o.as<int32_t>(), g->o2n.as<int32_t>(), g->col_ptr.as<int32_t>(),
-            g->row_idx.as<int32_t>(), g->csc_eid.as<int32_t>(), g->r_col_ptr.as<int32_t>(),
-            g->r_row_idx.as<int32_t>(), g->r_csc_eid.as<int32_t>());
-        note_launch();
+        const int64_t nchunks = (m + RL_SLOTS - 1) / RL_SLOTS;
+        Buf owner;
+        st = buf_alloc(g, owner, sizeof(int32_t) * (size_t)(nchunks + 1), s);
+        if (st == PR_OK) {
+            k_chunk_owner<<<(unsigned)((nchunks + 256) / 256), 256, 0, s>>>(
+                n, m, nchunks, g->r_col_ptr.as<int32_t>(), owner.as<int32_t>());
+            note_launch();
+            const unsigned rb = (unsigned)std::min<int64_t>((nchunks + 7) / 8, (int64_t)g->num_sms * 8);
+            k_relabel_lists<<<rb, 256, 0, s>>>(
+                m, nchunks, owner.as<int32_t>(), g->n2o.as<int32_t>(), g->o2n.as<int32_t>(),
+                g->col_ptr.as<int32_t>(), g->row_idx.as<int32_t>(), g->csc_eid.as<int32_t>(),
+                g->r_col_ptr.as<int32_t>(), g->r_row_idx.as<int32_t>(),
+                g->r_csc_eid.as<int32_t>());
+            note_launch();
+        }
+        drop_temp(g, owner, s);
     }
     drop_temp(g, k1, s);
     drop_temp(g, r_indeg, s);

@@ -245,28 +245,21 @@ extern "C" pr_status pr_scan_exclusive_noalloc(const int32_t *in, int32_t *out, 
 namespace fpr {
 
 // ------------------------------------------------------------- degrees
-// Out/in-degree histograms with warp-aggregated atomics (R-MAT hubs put many
-// edges of one warp on the same vertex); ids outside [0, n) raise err.
-__global__ void k_degrees(int64_t m, const int32_t *__restrict__ src,
-                          const int32_t *__restrict__ dst, int32_t n, int32_t *outdeg,
-                          int32_t *indeg, int32_t *err)
+// Degrees from keys sorted by one endpoint (the high or the low word): each
+// run of equal ids adds its length (end - start, written by the threads at
+// its two ends); with `low32` also the low words (the in-list sources).
+__global__ void k_run_degrees(int64_t m, const uint64_t *__restrict__ keys, int high,
+                              int32_t *deg, int32_t *low32)
 {
-    const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x; e0 < m; e0 += stride) {
-        int64_t e = e0 + threadIdx.x;
-        bool valid = e < m;
-        int s = valid ? src[e] : 0;
-        int t = valid ? dst[e] : 0;
-        bool ok = valid && s >= 0 && s < n && t >= 0 && t < n;
-        if (valid && !ok) atomicOr(err, 1);
-        unsigned okmask = __ballot_sync(FULL, ok);
-        if (ok) {
-            unsigned peers = __match_any_sync(okmask, s);
-            if (lane == __ffs(peers) - 1) atomicAdd(&outdeg[s], __popc(peers));
-            peers = __match_any_sync(okmask, t);
-            if (lane == __ffs(peers) - 1) atomicAdd(&indeg[t], __popc(peers));
-        }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const uint64_t k = keys[i];
+        const uint32_t v = high ? (uint32_t)(k >> 32) : (uint32_t)k;
+        if (low32) low32[i] = (int32_t)(uint32_t)k;
+        const bool first = i == 0 || (high ? (uint32_t)(keys[i - 1] >> 32) : (uint32_t)keys[i - 1]) != v;
+        const bool last = i == m - 1 || (high ? (uint32_t)(keys[i + 1] >> 32) : (uint32_t)keys[i + 1]) != v;
+        if (first) atomicSub(&deg[v], (int32_t)i);
+        if (last) atomicAdd(&deg[v], (int32_t)(i + 1));
     }
 }
 
@@ -379,8 +372,10 @@ __global__ void __launch_bounds__(RS_BS) k_radix_scatter(
 // `shifts`; alt_k/alt_v are same-size scratch.  Result ends in keys/vals.
 pr_status radix_sort(pr_graph *g, uint64_t *keys, int32_t *vals, uint64_t *alt_k,
                             int32_t *alt_v, int64_t m, const std::vector<int> &shifts,
-                            cudaStream_t s)
+                            cudaStream_t s, uint64_t **kres, int32_t **vres)
 {
+    if (kres) *kres = keys;
+    if (vres) *vres = vals;
     if (m <= 1 || shifts.empty()) return PR_OK;
     int nblocks = (int)((m + RS_TILE - 1) / RS_TILE);
     int64_t ncount = (int64_t)256 * nblocks;
@@ -405,7 +400,10 @@ pr_status radix_sort(pr_graph *g, uint64_t *keys, int32_t *vals, uint64_t *alt_k
     }
     cudaError_t e = cudaGetLastError();
     if (st == PR_OK && e != cudaSuccess) st = cuda_status(e, "radix sort", __FILE__, __LINE__);
-    if (st == PR_OK && ka != keys) {
+    if (st == PR_OK && kres) {  // the caller takes the result where it ends
+        *kres = ka;
+        *vres = va;
+    } else if (st == PR_OK && ka != keys) {
         cudaError_t e1 = cudaMemcpyAsync(keys, ka, sizeof(uint64_t) * (size_t)m,
                                          cudaMemcpyDeviceToDevice, s);
         cudaError_t e2 = cudaMemcpyAsync(vals, va, sizeof(int32_t) * (size_t)m,
@@ -427,19 +425,18 @@ std::vector<int> digit_shifts(int32_t n, int offset)
     return out;
 }
 
+// key = (dst << 32) | src, value = input position; ids outside [0, n) set
+// bit 0 of err.
 __global__ void k_make_csc_keys(int64_t m, const int32_t *__restrict__ src,
-                                const int32_t *__restrict__ dst, uint64_t *keys, int32_t *vals)
+                                const int32_t *__restrict__ dst, int32_t n, uint64_t *keys,
+                                int32_t *vals, int32_t *err)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m) return;
-    keys[e] = ((uint64_t)(uint32_t)dst[e] << 32) | (uint64_t)(uint32_t)src[e];
+    const int32_t a = src[e], b = dst[e];
+    if (a < 0 || a >= n || b < 0 || b >= n) atomicOr(err, 1);
+    keys[e] = ((uint64_t)(uint32_t)b << 32) | (uint64_t)(uint32_t)a;
     vals[e] = (int32_t)e;
-}
-
-__global__ void k_split_keys(int64_t m, const uint64_t *__restrict__ keys, int32_t *low32)
-{
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m) low32[i] = (int32_t)(uint32_t)(keys[i] & 0xffffffffu);
 }
 
 // key = (source << 32) | destination for every in-list slot (warp per vertex)
