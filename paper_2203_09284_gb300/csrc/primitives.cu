@@ -12,6 +12,7 @@
 #include <atomic>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace fpr {
 
@@ -265,141 +266,217 @@ __global__ void k_run_degrees(int64_t m, const uint64_t *__restrict__ keys, int 
 
 // ----------------------------------------------------------- radix sort
 // Stable LSD radix sort of (64-bit key, int32 value) pairs, 8 bits a pass.
-// A block owns a tile of 4096 pairs; warp w owns the w-th 512-pair run and
-// ranks it in 16 rounds of 32 with __match_any_sync, so the order within a
-// tile is preserved; the tile is reordered by digit in shared memory before
-// it is written out.
+// Per pass: per-tile digit counts (tiles of 4096 pairs), one exclusive scan
+// of them in digit-major order (the output start of each (digit, tile)),
+// then the scatter: persistent blocks take tiles round-robin; a block ranks
+// its tile by digit (stable: warp w ranks the w-th 512-pair run in 16 rounds
+// of 32 with __match_any_sync), reorders it by digit in shared memory and
+// writes each digit's run to its place, while the bulk copy (TMA) of its
+// next tile lands in shared memory.  Every copy wait is bounded.
 constexpr int RS_BS = 256;
 constexpr int RS_ROUNDS = 16;
 constexpr int RS_TILE = RS_BS * RS_ROUNDS;
 constexpr int RS_WARPS = RS_BS / 32;
+constexpr int RS_BLOCKS_PER_SM = 2;
+constexpr uint32_t RS_WAIT_LIMIT = 1u << 22;
 
 __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t m, int shift,
-                             int32_t *counts, int nblocks)
+                             int32_t *counts, int64_t ntiles)
 {
     __shared__ int hist[256];
     hist[threadIdx.x] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t base = (int64_t)blockIdx.x * RS_TILE;
 #pragma unroll 4
     for (int j = 0; j < RS_ROUNDS; ++j) {
-        int64_t i = base + (int64_t)j * RS_BS + threadIdx.x;
+        const int64_t i = base + (int64_t)j * RS_BS + threadIdx.x;
         if (i < m) atomicAdd(&hist[(keys[i] >> shift) & 0xFF], 1);
     }
     __syncthreads();
-    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = hist[threadIdx.x];
+    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = hist[threadIdx.x];
 }
 
-// Ranks the tile's pairs by digit (stable), reorders them in shared memory,
-// then writes each digit's run to its place in the output, so consecutive
-// threads store consecutive addresses.
 struct RadixSmem {
-    uint64_t k[RS_TILE];
-    int32_t v[RS_TILE];
+    uint64_t ik[RS_TILE];  // next tile, landed by the bulk copy
+    int32_t iv[RS_TILE];
+    uint64_t ok[RS_TILE];  // the current tile reordered by digit
+    int32_t ov[RS_TILE];
     int wcnt[RS_WARPS][256];
     int bstart[256];
+    int dbase[256];  // output position of reordered slot q: dbase[digit] + q
     int sw[33];
+    uint64_t bar;
+    int bad;
 };
 
-__global__ void __launch_bounds__(RS_BS) k_radix_scatter(
+__global__ void __launch_bounds__(RS_BS, RS_BLOCKS_PER_SM) k_radix_scatter(
     const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     int32_t *__restrict__ vout, int64_t m, int shift, const int32_t *__restrict__ offsets,
-    int nblocks)
+    int32_t *err)
 {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     RadixSmem &sm = *reinterpret_cast<RadixSmem *>(rs_smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_BS) (&sm.wcnt[0][0])[i] = 0;
-    __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
-    const int64_t base = tile0 + (int64_t)warp * (RS_ROUNDS * 32);
-    const int nvalid = (int)min((int64_t)RS_TILE, m - tile0);
-    uint64_t k[RS_ROUNDS];
-    int32_t v[RS_ROUNDS];
-    int rank[RS_ROUNDS];
-#pragma unroll
-    for (int j = 0; j < RS_ROUNDS; ++j) {
-        int64_t i = base + j * 32 + lane;
-        bool valid = i < m;
-        k[j] = valid ? kin[i] : 0;
-        v[j] = valid ? vin[i] : 0;
-        int dg = (int)((k[j] >> shift) & 0xFF);
-        unsigned vmask = __ballot_sync(FULL, valid);
-        int before = 0, r = 0;
-        unsigned peers = 0;
-        if (valid) {
-            peers = __match_any_sync(vmask, dg);
-            r = __popc(peers & lt);
-            before = sm.wcnt[warp][dg];
+    const int64_t ntiles = (m + RS_TILE - 1) / RS_TILE;
+    auto is_full = [&](int64_t t) { return t < ntiles && (t + 1) * RS_TILE <= m; };
+    // a full tile arrives by bulk copy (16-byte aligned, 48 KB), the last
+    // partial one by plain loads
+    auto issue = [&](int64_t t) {
+        if (is_full(t)) {
+            mbar_expect_tx(&sm.bar, RS_TILE * 12);
+            bulk_load(sm.ik, kin + t * RS_TILE, RS_TILE * 8, &sm.bar);
+            bulk_load(sm.iv, vin + t * RS_TILE, RS_TILE * 4, &sm.bar);
         }
-        __syncwarp();
-        if (valid && r == 0) sm.wcnt[warp][dg] = before + __popc(peers);
-        __syncwarp();
-        rank[j] = valid ? before + r : -1;
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar, 1);
+        mbar_init_fence();
+        sm.bad = 0;
+        issue(blockIdx.x);
     }
     __syncthreads();
-    {   // exclusive prefix over warps for digit threadIdx.x, then over digits
-        int run = 0;
-#pragma unroll
-        for (int w = 0; w < RS_WARPS; ++w) {
-            int t = sm.wcnt[w][threadIdx.x];
-            sm.wcnt[w][threadIdx.x] = run;
-            run += t;
+    uint32_t parity = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t tile0 = t * RS_TILE;
+        const bool full = is_full(t);
+        const int nvalid = (int)min((int64_t)RS_TILE, m - tile0);
+        if (full) {
+            if (!mbar_wait(&sm.bar, parity, RS_WAIT_LIMIT)) {
+                atomicOr(err, 1);
+                sm.bad = 1;
+            }
+            parity ^= 1;
         }
-        sm.bstart[threadIdx.x] = block_exclusive_sum(run, sm.sw, nullptr);
-    }
-    __syncthreads();
+        for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_BS) (&sm.wcnt[0][0])[i] = 0;
+        // this tile's output start of digit threadIdx.x
+        const int dstart = offsets[(int64_t)threadIdx.x * ntiles + t];
+        uint64_t k[RS_ROUNDS];
+        int32_t v[RS_ROUNDS];
+        int rank[RS_ROUNDS];
 #pragma unroll
-    for (int j = 0; j < RS_ROUNDS; ++j) {
-        if (rank[j] < 0) continue;
-        const int dg = (int)((k[j] >> shift) & 0xFF);
-        const int q = sm.bstart[dg] + sm.wcnt[warp][dg] + rank[j];
-        sm.k[q] = k[j];
-        sm.v[q] = v[j];
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < nvalid; q += RS_BS) {
-        const uint64_t kk = sm.k[q];
-        const int dg = (int)((kk >> shift) & 0xFF);
-        const int64_t pos = (int64_t)offsets[(int64_t)dg * nblocks + blockIdx.x] + (q - sm.bstart[dg]);
-        kout[pos] = kk;
-        vout[pos] = sm.v[q];
+        for (int j = 0; j < RS_ROUNDS; ++j) {
+            const int q = warp * (RS_ROUNDS * 32) + j * 32 + lane;
+            const bool valid = q < nvalid;
+            k[j] = valid ? (full ? sm.ik[q] : kin[tile0 + q]) : 0;
+            v[j] = valid ? (full ? sm.iv[q] : vin[tile0 + q]) : 0;
+        }
+        __syncthreads();  // input buffer read, counters zero
+        if (sm.bad) {
+            // the copy did not land in time: wait once more (bounded) for it
+            // before leaving, so nothing is in flight at exit
+            mbar_wait(&sm.bar, parity ^ 1, RS_WAIT_LIMIT);
+            break;
+        }
+        if (threadIdx.x == 0) {
+            fence_async_smem();
+            issue(t + gridDim.x);
+        }
+#pragma unroll
+        for (int j = 0; j < RS_ROUNDS; ++j) {
+            const bool valid = warp * (RS_ROUNDS * 32) + j * 32 + lane < nvalid;
+            const int dg = (int)((k[j] >> shift) & 0xFF);
+            const unsigned vmask = __ballot_sync(FULL, valid);
+            int before = 0, r = 0;
+            unsigned peers = 0;
+            if (valid) {
+                peers = __match_any_sync(vmask, dg);
+                r = __popc(peers & lt);
+                before = sm.wcnt[warp][dg];
+            }
+            __syncwarp();
+            if (valid && r == 0) sm.wcnt[warp][dg] = before + __popc(peers);
+            __syncwarp();
+            rank[j] = valid ? before + r : -1;
+        }
+        __syncthreads();
+        {   // digit d = threadIdx.x: prefix over warps, then over digits
+            const int d = threadIdx.x;
+            int run = 0;
+#pragma unroll
+            for (int w = 0; w < RS_WARPS; ++w) {
+                const int c = sm.wcnt[w][d];
+                sm.wcnt[w][d] = run;
+                run += c;
+            }
+            const int bst = block_exclusive_sum(run, sm.sw, nullptr);
+            sm.bstart[d] = bst;
+            sm.dbase[d] = dstart - bst;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < RS_ROUNDS; ++j) {
+            if (rank[j] < 0) continue;
+            const int dg = (int)((k[j] >> shift) & 0xFF);
+            const int q = sm.bstart[dg] + sm.wcnt[warp][dg] + rank[j];
+            sm.ok[q] = k[j];
+            sm.ov[q] = v[j];
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < nvalid; q += RS_BS) {
+            const uint64_t kk = sm.ok[q];
+            const int64_t pos = (int64_t)sm.dbase[(kk >> shift) & 0xFF] + q;
+            if (pos >= 0 && pos < m) {
+                kout[pos] = kk;
+                vout[pos] = sm.ov[q];
+            }
+        }
+        __syncthreads();  // reordered tile and counters free for the next tile
     }
 }
 
-// Sorts (keys, vals) in place by the 8-bit digits starting at each shift in
-// `shifts`; alt_k/alt_v are same-size scratch.  Result ends in keys/vals.
+// Sorts (keys, vals) by the 8-bit digits starting at each shift in `shifts`;
+// alt_k/alt_v are same-size scratch.  The result ends in keys/vals unless
+// kres/vres are given (then it stays where the last pass wrote it).
 pr_status radix_sort(pr_graph *g, uint64_t *keys, int32_t *vals, uint64_t *alt_k,
-                            int32_t *alt_v, int64_t m, const std::vector<int> &shifts,
-                            cudaStream_t s, uint64_t **kres, int32_t **vres)
+                     int32_t *alt_v, int64_t m, const std::vector<int> &shifts, cudaStream_t s,
+                     uint64_t **kres, int32_t **vres)
 {
     if (kres) *kres = keys;
     if (vres) *vres = vals;
     if (m <= 1 || shifts.empty()) return PR_OK;
-    int nblocks = (int)((m + RS_TILE - 1) / RS_TILE);
-    int64_t ncount = (int64_t)256 * nblocks;
-    Buf counts;
-    PR_TRY(buf_alloc(g, counts, sizeof(int32_t) * (size_t)(ncount + 1), s));
-    static_assert(sizeof(RadixSmem) <= 96 * 1024, "radix tile exceeds shared memory");
-    PR_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_radix_scatter),
+    if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals) |
+         reinterpret_cast<uintptr_t>(alt_k) | reinterpret_cast<uintptr_t>(alt_v)) & 15) {
+        set_error("radix_sort: buffers must be 16-byte aligned (bulk copies)");
+        return PR_ERR_INVALID_ARG;
+    }
+    const int64_t ntiles = (m + RS_TILE - 1) / RS_TILE;
+    const int64_t ncount = 256 * ntiles;
+    // scratch: counts [256][ntiles] (+ total), error word
+    Buf scratch;
+    PR_TRY(buf_alloc(g, scratch, sizeof(int32_t) * (size_t)(ncount + 2), s));
+    int32_t *counts = scratch.as<int32_t>();
+    int32_t *err = counts + ncount + 1;
+    pr_status st = PR_OK;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_radix_scatter),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(RadixSmem)));
+                                 (int)sizeof(RadixSmem));
     uint64_t *ka = keys, *kb = alt_k;
     int32_t *va = vals, *vb = alt_v;
-    pr_status st = PR_OK;
-    for (int sh : shifts) {
-        k_radix_hist<<<nblocks, RS_BS, 0, s>>>(ka, m, sh, counts.as<int32_t>(), nblocks); note_launch();
-        st = scan_exclusive(g, counts.as<int32_t>(), counts.as<int32_t>(), ncount, s);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)g->num_sms * RS_BLOCKS_PER_SM);
+    for (size_t p = 0; p < shifts.size() && e == cudaSuccess && st == PR_OK; ++p) {
+        k_radix_hist<<<(unsigned)ntiles, RS_BS, 0, s>>>(ka, m, shifts[p], counts, ntiles);
+        note_launch();
+        st = scan_exclusive(g, counts, counts, ncount, s);
         if (st != PR_OK) break;
-        k_radix_scatter<<<nblocks, RS_BS, sizeof(RadixSmem), s>>>(ka, va, kb, vb, m, sh,
-                                                                  counts.as<int32_t>(), nblocks);
+        k_radix_scatter<<<grid, RS_BS, sizeof(RadixSmem), s>>>(ka, va, kb, vb, m, shifts[p],
+                                                             counts, err);
         note_launch();
         std::swap(ka, kb);
         std::swap(va, vb);
+        e = cudaGetLastError();
     }
-    cudaError_t e = cudaGetLastError();
+    int32_t herr = 0;
+    if (st == PR_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(&herr, err, sizeof(herr), cudaMemcpyDeviceToHost, s);
+    if (st == PR_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (st == PR_OK && e != cudaSuccess) st = cuda_status(e, "radix sort", __FILE__, __LINE__);
+    if (st == PR_OK && herr) {
+        set_error("radix_sort: a bounded copy wait gave up");
+        st = PR_ERR_TIMEOUT;
+    }
     if (st == PR_OK && kres) {  // the caller takes the result where it ends
         *kres = ka;
         *vres = va;
@@ -411,8 +488,8 @@ pr_status radix_sort(pr_graph *g, uint64_t *keys, int32_t *vals, uint64_t *alt_k
         if (e1 != cudaSuccess || e2 != cudaSuccess)
             st = cuda_status(e1 != cudaSuccess ? e1 : e2, "radix copy", __FILE__, __LINE__);
     }
-    g->owned.erase(std::remove(g->owned.begin(), g->owned.end(), &counts), g->owned.end());
-    buf_free(g, counts, s);
+    g->owned.erase(std::remove(g->owned.begin(), g->owned.end(), &scratch), g->owned.end());
+    buf_free(g, scratch, s);
     return st;
 }
 
