@@ -126,6 +126,7 @@ struct Items {
                                   // (KB; <= 0: none)
     int32_t wait_limit = 0;       // copy-barrier polls before a timeout (0: default)
     int32_t test_stall = 0;       // testing only: force the timeout path
+    int32_t fused_split = 0;      // fused sweep launches (pr_tune.fused_split)
     Buf hubseg_start;             // [nhub + 1] first segment of each hub
     Buf seg_acc;                  // [nhubseg] double partial sums
     Buf hub_cnt;                  // [nhub] segments finished this sweep

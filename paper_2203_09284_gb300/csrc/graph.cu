@@ -227,7 +227,9 @@ pr_tune effective_tune(const pr_graph *g, const pr_tune *t)
         r.deterministic_gs = t->deterministic_gs;
         r.wait_limit = t->wait_limit > 0 ? t->wait_limit : 0;
         r.test_stall = t->test_stall ? 1 : 0;
+        r.fused_split = t->fused_split;
     }
+    r.fused_split = std::max(0, std::min(r.fused_split, 2));
     r.stage_kb = r.stage_kb < 0 ? -1 : std::min(r.stage_kb, 227);
     // a low tile's in-edges (at most tile + t_lo) sit in one warp's slice of
     // shared memory, and a lane adds up to t_lo of them
@@ -274,6 +276,7 @@ pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
     it.stage_kb = t.stage_kb;
     it.wait_limit = t.wait_limit;
     it.test_stall = t.test_stall;
+    it.fused_split = t.fused_split;
     if (it.t_lo == t.t_lo && it.t_hub == t.t_hub && it.hub_seg == t.hub_seg &&
         it.tile_c == t.tile)
         return PR_OK;

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "solve_impl.cuh"
@@ -134,10 +135,16 @@ pr_status make_plan(pr_graph *g, const SweepParams &p, bool gs, SweepPlan &plan)
     plan.func = pick_sweep<T, A>(gs, p.ew != nullptr);
     plan.smem = gs ? layout_of<T, A, true>(p).total : layout_of<T, A, false>(p).total;
     // fused sweep: the hottest items (hub segments and the widest mid
-    // groups) first, so the rest reads their new values
+    // groups) first, so the rest reads their new values; in one launch
+    // where pr_tune.fused_split asks for it (by default the FP32- and
+    // BF16-stored correction sweeps)
     const int total = p.nhubseg + p.mi[4] + p.nlt;
     const int split = p.nhubseg + p.mi[1];
-    if (gs && split > 0 && split < total) {
+    const int fs = g->items.fused_split;
+    const bool one = fs == 2 || (fs == 0 && p.dc &&
+                                 (std::is_same<T, float>::value ||
+                                  std::is_same<T, __nv_bfloat16>::value));
+    if (gs && !one && split > 0 && split < total) {
         plan.nlaunch = 2;
         plan.p[0] = p;
         plan.p[0].item_lo = 0;
@@ -370,7 +377,7 @@ pr_status prepare_solve(pr_graph *g, const pr_options *o, pr_tune &tn, cudaStrea
     const Items &it = g->items;
     if (it.t_lo != tn.t_lo || it.t_hub != tn.t_hub || it.hub_seg != tn.hub_seg ||
         it.tile_c != tn.tile || it.stage_kb != tn.stage_kb || it.wait_limit != tn.wait_limit ||
-        it.test_stall != tn.test_stall)
+        it.test_stall != tn.test_stall || it.fused_split != tn.fused_split)
         release_graphs(g);  // cached loops hold the old launch parameters
     PR_TRY(ensure_items(g, tn, s));
     PR_TRY(ensure_workspace(g, s));

@@ -106,6 +106,20 @@ def test_defect_correction_reaches_fp64_accuracy(s16, precision, variant, use_gr
     assert abs(xs.sum() - 1) < 1e-13
 
 
+@pytest.mark.parametrize("fused_split", [1, 2])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_dc", "fp16_dc"])
+def test_fused_split_reaches_the_fixed_point(s16, fused_split, precision):
+    """Both launch plans of the fused sweep (hot items first, or one launch)
+    converge to the same fixed point; only the sweep count may differ."""
+    n, src, dst, og, g, star = s16
+    x, r = g.solve(variant="gs", precision=precision, threshold=1e-10,
+                   tune={"fused_split": fused_split})
+    assert r.status == 0, (r.iters, r.outer_iters, r.residual)
+    xs = x.cpu().numpy()
+    assert l1(xs, star.x) <= (BOUND if precision == "fp64" else DC_BOUND)
+    assert top_order_matches(xs, star.x)
+
+
 def test_linf_norm_and_not_converged(s16):
     n, src, dst, og, g, star = s16
     x, r = g.solve(norm="linf", threshold=1e-14, max_iter=500)
