@@ -280,6 +280,8 @@ constexpr int RS_WARPS = RS_BS / 32;
 constexpr int RS_BLOCKS_PER_SM = 2;
 constexpr uint32_t RS_WAIT_LIMIT = 1u << 22;
 
+// Digit counts of tile blockIdx.x: all 16 keys of a thread are loaded
+// (streaming, read once) before the shared-memory increments.
 __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t m, int shift,
                              int32_t *counts, int64_t ntiles)
 {
@@ -287,11 +289,15 @@ __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t m, int s
     hist[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-#pragma unroll 4
+    int dg[RS_ROUNDS];
+#pragma unroll
     for (int j = 0; j < RS_ROUNDS; ++j) {
         const int64_t i = base + (int64_t)j * RS_BS + threadIdx.x;
-        if (i < m) atomicAdd(&hist[(keys[i] >> shift) & 0xFF], 1);
+        dg[j] = i < m ? (int)((__ldcs(keys + i) >> shift) & 0xFF) : -1;
     }
+#pragma unroll
+    for (int j = 0; j < RS_ROUNDS; ++j)
+        if (dg[j] >= 0) atomicAdd(&hist[dg[j]], 1);
     __syncthreads();
     counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = hist[threadIdx.x];
 }
