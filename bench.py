@@ -41,8 +41,8 @@ METRIC = "R-MAT-22 time to L1<1e-10 and GTEPS (% HBM peak), mixed/fused vs plain
 # workload, from the ncu capture summarised in profiles/ (see the command
 # there); reported only while the sweep's sources are the ones captured.
 SWEEP_TRAFFIC = {
-    "sources_sha256": "0df6e581f99c806aa62d7e16f4c632fb2c75ed71f6575a9a606ef54cfd0ac9c0",
-    "bytes": 343113472,  # 338,799,104 read + 4,314,368 written
+    "sources_sha256": "984275afcfb42aa85dee6a91e0ee054709e4d0e6234dcd9e59319fd5d7517668",
+    "bytes": 342882560,  # 338,829,312 read + 4,053,248 written
 }
 SWEEP_SOURCES = ("sweep.cuh", "tma.cuh", "common.cuh")
 
