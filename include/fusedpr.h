@@ -164,10 +164,14 @@ pr_status pr_options_default(pr_options *o);
  * Results of every solve are returned in the input ids.
  *   n       vertices, >= 1
  *   m       edges, 0 <= m < 2^31
- *   src,dst device int32 [m]; ids must lie in [0, n) (checked on the
+ *   src,dst int32 [m] in device (or managed) memory, or in page-locked host
+ *           memory, which the build reads once over the host link (no
+ *           separate copy); pageable host memory is refused
+ *           (PR_ERR_INVALID_ARG).  Ids must lie in [0, n) (checked on the
  *           device: PR_ERR_INVALID_ARG otherwise).  Self-loops and repeated
  *           edges are kept as ordinary edges.
- *   w       device float [m] raw positive edge weights, or NULL (unweighted).
+ *   w       float [m] raw positive edge weights (same memory rules), or NULL
+ *           (unweighted).
  *           Weighted graphs use P_uv = w_uv / sum_v' w_uv'.
  *   flags   PR_BUILD_CSR also builds the out-lists (needed by pr_backward;
  *           built lazily otherwise).

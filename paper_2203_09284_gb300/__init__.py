@@ -198,14 +198,20 @@ def torch_allocator() -> PrAllocator:
     return _TORCH_ALLOCATOR
 
 
+def _device_readable(t):
+    return t.is_cuda or (t.device.type == "cpu" and t.is_pinned())
+
+
 def pr_graph_create(n, src, dst, w=None, flags=0, allocator=None, stream=None):
-    """Builds a graph from int32 device tensors src/dst (and optional float32
-    weights).  Returns an opaque handle (int)."""
+    """Builds a graph from int32 tensors src/dst (and optional float32
+    weights) on the device or in pinned host memory (read once by the build,
+    no separate copy).  Returns an opaque handle (int)."""
     for t, name in ((src, "src"), (dst, "dst")):
-        if not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
-            raise ValueError(f"{name} must be a contiguous int32 CUDA tensor")
-    if w is not None and not (w.is_cuda and w.dtype == torch.float32 and w.is_contiguous()):
-        raise ValueError("w must be a contiguous float32 CUDA tensor")
+        if not (_device_readable(t) and t.dtype == torch.int32 and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous int32 CUDA or pinned host tensor")
+    if w is not None and not (_device_readable(w) and w.dtype == torch.float32
+                              and w.is_contiguous()):
+        raise ValueError("w must be a contiguous float32 CUDA or pinned host tensor")
     out = ctypes.c_void_p()
     alloc = ctypes.byref(allocator) if allocator is not None else None
     st = lib().pr_graph_create(int(n), int(src.numel()), _ptr(src), _ptr(dst), _ptr(w),
@@ -326,7 +332,8 @@ def pr_backward(handle, options, x, grad_x, grad_w=None, grad_d=None, stream=Non
 
 
 class Graph:
-    """Owns a pr_graph handle built from device edge tensors."""
+    """Owns a pr_graph handle built from edge tensors on the device or in
+    pinned host memory."""
 
     def __init__(self, n, src, dst, w=None, build_csr=False, use_torch_allocator=True,
                  stream=None):

@@ -631,7 +631,7 @@ static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, 
                         std::make_pair(&g->p64_csc, sizeof(double) * ((size_t)m + 16)),
                         std::make_pair(&g->p32_csc, sizeof(float) * ((size_t)m + 16))})
             PR_TRY(buf_alloc(g, *pb.first, pb.second, s));
-        PR_CUDA(cudaMemcpyAsync(g->w.p, w, sizeof(float) * (size_t)m, cudaMemcpyDeviceToDevice, s));
+        PR_CUDA(cudaMemcpyAsync(g->w.p, w, sizeof(float) * (size_t)m, cudaMemcpyDefault, s));
         k_rowsum<<<(n + 255) / 256, 256, 0, s>>>(n, g->row_ptr.as<int32_t>(),
                                                  g->csr_eid.as<int32_t>(), g->w.as<float>(),
                                                  g->rowsum.as<double>());
@@ -671,6 +671,28 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
     if (alloc && (!alloc->alloc || !alloc->free)) {
         set_error("pr_graph_create: allocator hooks incomplete");
         return PR_ERR_INVALID_ARG;
+    }
+    // the edge arrays are read by kernels: device (or managed) memory, or
+    // page-locked host memory, which the kernels read over the host link
+    // through its device address; pageable host memory is refused
+    if (m > 0) {
+        const void *in[3] = {src, dst, w};
+        const void *dev[3] = {nullptr, nullptr, nullptr};
+        for (int k = 0; k < 3; ++k) {
+            if (!in[k]) continue;
+            cudaPointerAttributes a;
+            if (cudaPointerGetAttributes(&a, in[k]) != cudaSuccess ||
+                a.type == cudaMemoryTypeUnregistered || !a.devicePointer) {
+                cudaGetLastError();
+                set_error("pr_graph_create: edge array %d is not device-accessible (device, managed "
+                          "or page-locked host memory)", k);
+                return PR_ERR_INVALID_ARG;
+            }
+            dev[k] = a.devicePointer;
+        }
+        src = static_cast<const int32_t *>(dev[0]);
+        dst = static_cast<const int32_t *>(dev[1]);
+        w = static_cast<const float *>(dev[2]);
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     pr_graph *g = new pr_graph();

@@ -74,3 +74,55 @@ def test_build_rejects_bad_ids():
 def test_build_full_size_rmat22():
     """R-MAT scale 22 (configuration of the web-like workload): bit-exact."""
     check_build(*gen.rmat(22, 16, seed=1, dangling_frac=0.10))
+
+
+# The edge sort works on tiles of 4096 pairs: full tiles arrive by bulk
+# copy, a last partial one by plain loads, and 2 resident blocks per SM take
+# tiles round-robin.  Edge counts on and around those boundaries, and more
+# tiles than resident blocks.
+@pytest.mark.parametrize("m", [1, 4095, 4096, 4097, 8192, 8193, 4096 * 700 + 3])
+def test_build_sort_tile_boundaries(m):
+    n, src, dst = gen.rmat(18, 16, seed=11)
+    assert len(src) >= m
+    check_build(n, src[:m], dst[:m])
+
+
+def test_build_sort_one_hot_digit():
+    # every key's low source and destination digits equal (one bucket per
+    # tile in those passes), ragged last tile
+    n, src, dst = gen.rmat(16, 16, seed=12)
+    m = 4096 * 5 + 11
+    check_build(n, (src[:m] % 256) * 256, (dst[:m] % 256) * 256)
+
+
+def test_build_from_pinned_host_arrays():
+    """Edge arrays in page-locked host memory are read by the build over the
+    host link: the same products as from device arrays (weighted too);
+    pageable host arrays are refused before any kernel reads them."""
+    import ctypes
+    import paper_2203_09284_gb300 as fp
+    n, src, dst = gen.rmat(15, 16, seed=5)
+    w = gen.edge_weights(len(src), seed=5)
+    for weights in (None, w):
+        g_dev = graph(n, src, dst, weights, build_csr=True)
+        pin = lambda a: torch.from_numpy(a).pin_memory()
+        g_pin = fp.Graph(n, pin(src), pin(dst), None if weights is None else pin(weights),
+                         build_csr=True)
+        a, b = g_dev.export(csr=True), g_pin.export(csr=True)
+        assert a.keys() == b.keys()
+        for k in a:
+            assert torch.equal(a[k], b[k]), k
+        x1, r1 = g_dev.solve(threshold=1e-10)
+        x2, r2 = g_pin.solve(threshold=1e-10)
+        assert r1.iters == r2.iters and torch.equal(x1, x2)
+        g_dev.close()
+        g_pin.close()
+    with pytest.raises(ValueError):
+        fp.Graph(n, torch.from_numpy(src), torch.from_numpy(dst))
+    out = ctypes.c_void_p()
+    st = fp.lib().pr_graph_create(int(n), int(len(src)), ctypes.c_void_p(src.ctypes.data),
+                                  ctypes.c_void_p(dst.ctypes.data), None, 0, None,
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                  ctypes.byref(out))
+    assert st == fp.PR_ERR_INVALID_ARG and not out.value
+
