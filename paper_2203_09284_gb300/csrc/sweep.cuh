@@ -400,10 +400,9 @@ __host__ __device__ constexpr uint32_t a16(size_t b) { return (uint32_t)((b + 15
 
 // Dynamic shared memory of a sweep block:
 //   [staged y[0, stage)] [barriers] [32 warp slices]
-// and of one warp slice: [gathered terms, lcap] and for the fused sweep
-// [in-tile source of each slot (int16, -1 if none), lcap].
+// and of one warp slice: [gathered terms, lcap].
 struct Layout {
-    uint32_t bars, warps, wvals, wsidx, wbytes, total;
+    uint32_t bars, warps, wvals, wbytes, total;
 };
 
 __host__ __device__ inline Layout make_layout(int lcap, int sa, int st, bool gs, int stage)
@@ -412,9 +411,9 @@ __host__ __device__ inline Layout make_layout(int lcap, int sa, int st, bool gs,
     L.bars = a16((size_t)stage * st);
     L.warps = L.bars + 32;
     L.wvals = 0;
-    L.wsidx = a16((size_t)lcap * sa);
-    L.wbytes = L.wsidx + (gs ? a16((size_t)lcap * 2) : 0);
+    L.wbytes = a16((size_t)lcap * sa);
     L.total = L.warps + SWEEP_WARPS * L.wbytes;
+    (void)gs;
     return L;
 }
 
@@ -551,7 +550,6 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
 {
     const int v0 = d.x, v1 = d.y, ea = d.z, eb = d.w;
     A *vals = reinterpret_cast<A *>(slice + L.wvals);
-    short *sidx = reinterpret_cast<short *>(slice + L.wsidx);
     const A *ew = static_cast<const A *>(p.ew);
     // inputs of this lane's first vertex, issued before the gathers
     int u = v0 + lane;
@@ -584,13 +582,10 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
             const int s = (c < 4 ? j0 : j1) + (c & 3);
             if (s >= ea && s < eb) {
                 vals[s - ea] = W ? ew[s] * got[c] : got[c];
-                if constexpr (GS)
-                    sidx[s - ea] = (v[c] >= v0 && v[c] < v1) ? (short)(v[c] - v0) : (short)-1;
             }
         }
     }
     __syncwarp();
-    T *yself = static_cast<T *>(const_cast<T *>(src.y));
     for (int u0 = v0; u0 < v1; u0 += 32) {
         u = u0 + lane;
         if (u < v1) {
@@ -608,20 +603,7 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
                 r = rhs_of<A>(p, u, fin.base());
             }
             A acc = 0;
-            for (int i = a - ea; i < e - ea; ++i) {
-                A val = vals[i];
-                if constexpr (GS) {
-                    // a source of this tile updated in an earlier round of
-                    // this sweep: its new value (written before the last
-                    // __syncwarp, so visible to this lane)
-                    const int t = sidx[i];
-                    if (t >= 0 && v0 + t < u0) {
-                        const A nv = to_a<A>(ld_l2<T>(yself, v0 + t));
-                        val = W ? ew[ea + i] * nv : nv;
-                    }
-                }
-                acc += val;
-            }
+            for (int i = a - ea; i < e - ea; ++i) acc += vals[i];
             fin(u, acc, od, inv, yo, r);
         }
         __syncwarp();
