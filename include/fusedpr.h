@@ -292,7 +292,8 @@ pr_status pr_scan_exclusive_noalloc(const int32_t *in, int32_t *out, int64_t cou
  * first `hot` entries of y read from shared memory, one 1024-thread block
  * per SM).  Timed by the caller, it gives the rate at which this device
  * serves the sweep's irregular gathers alone.
- *   idx   device int32 [m], 16-byte aligned, every entry in [0, n)
+ *   idx   device int32 [m], 16-byte aligned (PR_ERR_INVALID_ARG otherwise);
+ *         an entry outside [0, n) gathers y[0] instead
  *   y     device float [n];  hot: 0 <= hot <= min(n, 49152)
  *   sink  device float [1], accumulated with atomics
  * Returns without synchronising.

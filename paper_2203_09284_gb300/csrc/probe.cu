@@ -13,7 +13,7 @@ constexpr int PROBE_BS = 1024;
 
 __global__ void __launch_bounds__(PROBE_BS, 1)
     k_gather_probe(const int32_t *__restrict__ idx, int64_t m, const float *__restrict__ y,
-                   int32_t hot, float *sink)
+                   int32_t n, int32_t hot, float *sink)
 {
     extern __shared__ float sy[];
     for (int i = threadIdx.x; i < hot; i += blockDim.x) sy[i] = y[i];
@@ -33,7 +33,10 @@ __global__ void __launch_bounds__(PROBE_BS, 1)
             asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0, %1, %2, %3}, [%4], %5;"
                 : "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
                 : "l"(idx + 4 * (q + stride)), "l"(pol));
-        const int v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        // an entry outside [0, n) reads y[0] instead (never out of bounds)
+        int v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = (unsigned)v[c] < (unsigned)n ? v[c] : 0;
         float got[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c)
@@ -41,8 +44,10 @@ __global__ void __launch_bounds__(PROBE_BS, 1)
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc += got[c];
     }
-    for (int64_t j = 4 * nq + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride)
-        acc += __ldg(y + idx[j]);
+    for (int64_t j = 4 * nq + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+        const int v = idx[j];
+        acc += __ldg(y + ((unsigned)v < (unsigned)n ? v : 0));
+    }
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) atomicAdd(sink, acc);
 }
@@ -59,6 +64,10 @@ extern "C" pr_status pr_gather_probe(const int32_t *idx, int64_t m, const float 
         set_error("pr_gather_probe: need m >= 0, n >= 1, 0 <= hot <= min(n, 49152) and buffers");
         return PR_ERR_INVALID_ARG;
     }
+    if (reinterpret_cast<uintptr_t>(idx) & 15) {  // 16-byte index loads
+        set_error("pr_gather_probe: idx must be 16-byte aligned");
+        return PR_ERR_INVALID_ARG;
+    }
     int dev = 0, sms = 0;
     PR_CUDA(cudaGetDevice(&dev));
     PR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -66,7 +75,7 @@ extern "C" pr_status pr_gather_probe(const int32_t *idx, int64_t m, const float 
     PR_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_gather_probe),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    k_gather_probe<<<sms, PROBE_BS, smem, s>>>(idx, m, y, hot, sink);
+    k_gather_probe<<<sms, PROBE_BS, smem, s>>>(idx, m, y, n, hot, sink);
     note_launch();
     PR_CUDA(cudaGetLastError());
     return PR_OK;
