@@ -158,8 +158,9 @@ def dist_backend():
 def measure_rows(dev, stream, peak, timed):
     """The other rows of the hot path, each timed with CUDA events on its
     stream (outside the headline step): batched personalised PageRank at
-    R-MAT scale 20 with 256 teleports, 64 uneven graphs solved together, and
-    the adjoint with gradients at scale 18."""
+    R-MAT scale 20 with 256 teleports, 64 uneven graphs solved together, the
+    adjoint with gradients at scale 18, and the scale-25 graph in FP64 and
+    with FP32/BF16/FP16-stored corrections."""
     import numpy as np
     import torch
 
@@ -238,6 +239,27 @@ def measure_rows(dev, stream, peak, timed):
                      "forward_ms": round(fms, 3), "forward_sweeps": fr.iters}
     g.close()
     rows["adjoint"] = row
+
+    # crawl-sized graph: R-MAT scale 25 (33.5M vertices, ~537M edges), FP64
+    # against FP32 sweeps with BF16-, FP16- and FP32-stored corrections
+    n, s_h, d_h = gen.rmat(25, 16, seed=1)
+    m = len(s_h)
+    s_d, d_d = torch.from_numpy(s_h).to(dev), torch.from_numpy(d_h).to(dev)
+    del s_h, d_h
+    build_ms, g = timed(lambda: fp.Graph(n, s_d, d_d), 1)
+    del s_d, d_d
+    x = torch.empty(n, dtype=torch.float64, device=dev)
+    row = {"workload": "rmat25_ef16_seed1", "n": n, "edges": m, "threshold": 1e-10,
+           "build_ms": round(build_ms, 2)}
+    for prec in ("fp64", "fp32_dc", "bf16_dc", "fp16_dc"):
+        ms, (_, r) = timed(lambda: g.solve(out=x, variant="jacobi", precision=prec,
+                                           threshold=1e-10, max_iter=1000), 2)
+        row[prec] = {"ms": round(ms, 2), "iters": r.iters, "outer": r.outer_iters,
+                     "residual": r.residual, "status": r.status}
+    g.close()
+    del x
+    torch.cuda.empty_cache()
+    rows["rmat25"] = row
     return rows
 
 
