@@ -111,14 +111,14 @@ typedef struct {
                           also wait on a barrier nothing arrives at, so the
                           timeout path runs (the solve returns
                           PR_ERR_TIMEOUT and the device stays usable) */
-    int32_t fused_split; /* launches of one fused sweep: 1 two (the hub
-                          segments and the widest mid groups first, so the
-                          rest reads their new values), 2 one, 0 (default)
-                          two except for the correction sweeps of
-                          PR_FP32_DC and PR_BF16_DC, which measured fewer
-                          sweeps to converge in one launch.  Changes which
-                          values a fused sweep reads fresh, hence its sweep
-                          count, not the fixed point. */
+    int32_t fused_split; /* launches of one fused sweep: 0 (default) or 1
+                          two (the hub segments and the widest mid groups
+                          first, so the rest reads their new values; with a
+                          4- or 2-byte stored vector the first launch writes
+                          its new values aside and they are copied in
+                          before the second), 2 one.  Changes which values
+                          a fused sweep reads fresh, hence its sweep count,
+                          not the fixed point. */
 } pr_tune;
 
 typedef struct {

@@ -462,7 +462,7 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     PR_CUDA(cudaStreamSynchronize(s));
     if (graph_loop)  // residual and update kernels per outer step, the inner sweeps
         note_launch((uint64_t)2 * hs[0].outer_iter +
-                    (uint64_t)(L.inner.nlaunch + (L.f_shift ? 1 : 0)) *
+                    (uint64_t)(plan_launches(L.inner) + (L.f_shift ? 1 : 0)) *
                         (hs[0].iter - hs[0].outer_iter));
     pr_status st = (pr_status)hs[0].status;
     if (res) {

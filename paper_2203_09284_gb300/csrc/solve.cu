@@ -9,7 +9,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <type_traits>
 
 #include "common.cuh"
 #include "solve_impl.cuh"
@@ -135,21 +134,32 @@ pr_status make_plan(pr_graph *g, const SweepParams &p, bool gs, SweepPlan &plan)
     plan.func = pick_sweep<T, A>(gs, p.ew != nullptr);
     plan.smem = gs ? layout_of<T, A, true>(p).total : layout_of<T, A, false>(p).total;
     // fused sweep: the hottest items (hub segments and the widest mid
-    // groups) first, so the rest reads their new values; in one launch
-    // where pr_tune.fused_split asks for it (by default the FP32- and
-    // BF16-stored correction sweeps)
+    // groups) first, so the rest reads their new values; one launch only
+    // where pr_tune.fused_split asks for it
     const int total = p.nhubseg + p.mi[4] + p.nlt;
     const int split = p.nhubseg + p.mi[1];
-    const int fs = g->items.fused_split;
-    const bool one = fs == 2 || (fs == 0 && p.dc &&
-                                 (std::is_same<T, float>::value ||
-                                  std::is_same<T, __nv_bfloat16>::value));
+    const bool one = g->items.fused_split == 2;
     if (gs && !one && split > 0 && split < total) {
         plan.nlaunch = 2;
         plan.p[0] = p;
         plan.p[0].item_lo = 0;
         plan.p[0].item_hi = split;
         plan.p[0].close = 0;
+        // 4- and 2-byte stored vectors: the first launch's vertices,
+        // [0, mb[1]), write their new values to y1 (so that launch gathers
+        // from an array nobody writes) and a copy puts them into y0 before
+        // the second launch; FP64 sweeps update in place (the copy bought
+        // them no time and cost two sweeps)
+        if (sizeof(T) < 8) {
+            plan.p[0].write_alt = 1;
+            plan.copy_func = reinterpret_cast<const void *>(&k_copy_front<T>);
+            plan.copy_n = g->items.mb[1];
+            plan.copy_grid =
+                (unsigned)std::max(1, std::min((plan.copy_n + 255) / 256, g->num_sms * 4));
+            plan.copy_st = p.st;
+            plan.copy_src = p.y1;
+            plan.copy_dst = p.y0;
+        }
         plan.p[1] = p;
         plan.p[1].item_lo = split;
         plan.p[1].item_hi = total;
@@ -191,6 +201,16 @@ pr_status add_plan_nodes(cudaGraph_t body, SweepPlan &plan, cudaGraphConditional
         cudaGraphNode_t node;
         PR_CUDA(cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
         prev = node;
+        if (k == 0 && plan.nlaunch > 1 && plan.copy_func) {
+            void *cargs[] = {&plan.copy_st, &plan.copy_src, &plan.copy_dst, &plan.copy_n};
+            cudaKernelNodeParams cp = {};
+            cp.func = const_cast<void *>(plan.copy_func);
+            cp.gridDim = dim3(plan.copy_grid);
+            cp.blockDim = dim3(256);
+            cp.kernelParams = cargs;
+            PR_CUDA(cudaGraphAddKernelNode(&node, body, &prev, 1, &cp));
+            prev = node;
+        }
     }
     if (last) *last = prev;
     return PR_OK;
@@ -204,6 +224,11 @@ pr_status launch_plan(SweepPlan &plan, cudaStream_t s)
         PR_CUDA(cudaLaunchKernel(plan.func, dim3(plan.grid[k]), dim3(plan.block), args,
                                  plan.smem, s));
         note_launch();
+        if (k == 0 && plan.nlaunch > 1 && plan.copy_func) {
+            void *cargs[] = {&plan.copy_st, &plan.copy_src, &plan.copy_dst, &plan.copy_n};
+            PR_CUDA(cudaLaunchKernel(plan.copy_func, dim3(plan.copy_grid), dim3(256), cargs, 0, s));
+            note_launch();
+        }
     }
     return PR_OK;
 }
@@ -365,7 +390,7 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
     PR_LAUNCH_CHECK();
     pr_status st = finish_result(g, res, s, 0);
     // loop sweeps + the launch that sees the stop flag
-    if (graph_loop) note_launch((uint64_t)plan.nlaunch * (g->host_state->iter + 1));
+    if (graph_loop) note_launch((uint64_t)plan_launches(plan) * (g->host_state->iter + 1));
     return st;
 }
 

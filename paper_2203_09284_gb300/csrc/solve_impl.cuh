@@ -22,8 +22,9 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs);
 unsigned sweep_grid(const pr_graph *g, int nitems, const void *func, size_t smem);
 
 // The launches of one sweep: one launch over all items, or for the fused
-// sweep the hub segments first and then the rest (so the second launch's
-// staged copy holds the new hub values).
+// sweep the hub segments and widest mid groups first, writing their new
+// values aside, a copy of those into the stored vector, then the rest (so
+// the second launch, its staged copy included, reads the new values).
 struct SweepPlan {
     const void *func = nullptr;
     size_t smem = 0;
@@ -31,7 +32,19 @@ struct SweepPlan {
     unsigned block = SWEEP_BS;
     unsigned grid[2] = {0, 0};
     SweepParams p[2];
+    // copy between the two launches (copy_func null: none)
+    const void *copy_func = nullptr;
+    unsigned copy_grid = 0;
+    const SolveState *copy_st = nullptr;
+    const void *copy_src = nullptr;
+    void *copy_dst = nullptr;
+    int32_t copy_n = 0;
 };
+// kernel launches of one sweep of the plan
+inline int plan_launches(const SweepPlan &plan)
+{
+    return plan.nlaunch + (plan.nlaunch > 1 && plan.copy_func ? 1 : 0);
+}
 template <typename T, typename A>
 pr_status make_plan(pr_graph *g, const SweepParams &p, bool gs, SweepPlan &plan);
 // adds the plan's launches as a chain of kernel nodes of `body` (the last

@@ -87,6 +87,7 @@ struct SweepParams {
     int32_t lcap;                 // per-warp slots for a low tile's in-edges
     int32_t stage;                // y[0, stage) is copied to shared memory
     int32_t item_lo, item_hi;     // this launch's items [item_lo, item_hi)
+    int32_t write_alt;            // fused sweep: write the new values to y1, not y0
     int32_t close;                // this launch closes the sweep
     uint32_t wait_limit;
     int32_t test_stall;
@@ -699,7 +700,7 @@ __global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_sweep(SweepParams p)
     T *yout;
     if constexpr (GS) {
         yin = static_cast<const T *>(p.y0);
-        yout = static_cast<T *>(p.y0);
+        yout = static_cast<T *>(p.write_alt ? p.y1 : p.y0);
     } else {
         yin = static_cast<const T *>((iter & 1) ? p.y1 : p.y0);
         yout = static_cast<T *>((iter & 1) ? p.y0 : p.y1);
@@ -708,6 +709,19 @@ __global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_sweep(SweepParams p)
     run_items<T, A, GS, W>(p, yin, fin);
     block_partials<A>(st, fin.pt);
     if (p.close && last_block(st) && threadIdx.x < 32) close_sweep(p);
+}
+
+// Between the two launches of a fused sweep: the first launch's vertices
+// [0, n) wrote their new values to y1 (so that launch gathered from an array
+// nobody was writing); they join y0 here, before the second launch reads
+// them.  Nothing to do once the solve has stopped.
+template <typename T>
+__global__ void k_copy_front(const SolveState *st, const T *__restrict__ src, T *__restrict__ dst,
+                             int32_t n)
+{
+    if (st->done) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[i] = src[i];
 }
 
 // Fused sweep in strict increasing input-id order (Eq. 9 exactly): one warp,
