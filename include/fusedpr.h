@@ -107,10 +107,6 @@ typedef struct {
                           most the room the tiles leave) */
     int32_t wait_limit;/* polls of a copy barrier before a device-side wait
                           gives up with PR_ERR_TIMEOUT (0: 4M) */
-    int32_t test_stall;/* testing only: 1 makes each block's first wait
-                          also wait on a barrier nothing arrives at, so the
-                          timeout path runs (the solve returns
-                          PR_ERR_TIMEOUT and the device stays usable) */
     int32_t fused_split; /* launches of one fused sweep: 0 (default) or 1
                           two (the hub segments and the widest mid groups
                           first, so the rest reads their new values; with a
@@ -138,6 +134,12 @@ typedef struct {
                                BF16 3e-2); an inner solve also stops once its
                                change has not fallen for 8 sweeps */
     const pr_tune *tune;    /* NULL: the graph's defaults */
+    int32_t no_rescale;     /* PR_FUSED_GS with PR_FP64 / PR_FP32: 1 runs the
+                               literal Algorithm 2, with no rescale of the
+                               iterate to sum 1 after each sweep (the result
+                               is still normalised once at the end); 0
+                               (default) rescales.  Ignored by Jacobi and the
+                               *_DC forms. */
 } pr_options;
 
 typedef struct {

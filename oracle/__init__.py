@@ -323,51 +323,63 @@ def dense_pagerank(n, src, dst, d=0.85, w=None, tele=None, dangling_along_tele=F
 # Cancellation-free central differences (composition of the routines above)
 # ---------------------------------------------------------------------------
 
-def _perturbed_csc_p(g: Graph, w, eid, delta):
-    """P per in-list slot after raw weight w[eid] += delta (row renormalised)."""
-    w2 = np.array(w, dtype=np.float64)
-    w2[eid] += delta
+def _out_edges(g: Graph, eid):
+    """Source u of edge eid, u's out-edges (input ids, out-list order) and,
+    for every edge, its in-list slot."""
     u = int(g.src[eid])
-    lo, hi = int(g.row_ptr[u]), int(g.row_ptr[u + 1])
-    out_ids = g.csr_eid[lo:hi]
-    s = 0.0
-    for e in out_ids:  # out-list order, like orc_row_normalize
-        s += w2[e]
+    out_ids = g.csr_eid[int(g.row_ptr[u]):int(g.row_ptr[u + 1])]
     pos = np.empty(g.m, dtype=np.int64)
     pos[g.csc_eid] = np.arange(g.m)
-    return w2, u, out_ids, s, pos
+    return u, out_ids, pos
 
 
-def fd_weight(g: Graph, w, x, grad_x, eid, h=1e-6, d=0.85, csc_p=None):
+def fd_weight(g: Graph, w, x, grad_x, eid, h=1e-6, d=0.85, csc_p=None, with_bound=False):
     """Central difference of L = grad_x . x* w.r.t. raw weight w[eid], computed
     as g^T (x(w+h) - x(w-h)) / 2h where each half-difference is solved directly:
       (I - d M+) (x+ - x) = d (M+ - M) x,   (I - d M-) (x - x-) = d (M - M-) x.
     The right-hand sides live on the out-neighbours of the edge's source, so
-    there is no subtraction of two nearly equal solutions."""
+    there is no subtraction of two nearly equal solutions.
+    With with_bound, also returns a bound on the error the two stopped solves
+    leave in the result: each stops at an L1 change `err`, so its solution is
+    within d/(1-d) err of the exact one in L1 (d M is a 1-norm contraction
+    by d), and the quotient is off by at most |grad_x|_inf times their sum /
+    2h."""
     if csc_p is None:
         _, _, csc_p = row_normalize(g, w)
     total = np.zeros(g.n)
+    solve_err = 0.0
+    u, out_ids, pos = _out_edges(g, eid)
+    wf = [float(np.float64(np.float32(w[e]))) for e in out_ids]
+    s0 = 0.0
+    for we in wf:  # out-list order, like orc_row_normalize
+        s0 += we
     for sign in (+1.0, -1.0):
-        w2, u, out_ids, s2, pos = _perturbed_csc_p(g, w, eid, sign * h)
+        # raw weight w_e + delta: u's row sum becomes s0 + delta, and the
+        # change of each P_uv' is written without subtracting two nearly
+        # equal quotients:
+        #   (w_e + delta)/(s0 + delta) - w_e/s0 = delta (s0 - w_e) / (s0 s1)
+        #   w_e'/(s0 + delta) - w_e'/s0        = -w_e' delta / (s0 s1)
+        delta = sign * h
+        q = delta / (s0 * (s0 + delta))
         p2 = np.array(csc_p, dtype=np.float64)
-        s0 = 0.0
-        for e in out_ids:
-            s0 += float(np.float64(np.float32(w[e])))
         rhs = np.zeros(g.n)
-        for e in out_ids:
+        for e, we in zip(out_ids, wf):
             v = int(g.dst[e])
-            new = w2[e] / s2
-            old = float(np.float64(np.float32(w[e]))) / s0
-            p2[pos[e]] = new
-            rhs[v] += d * x[u] * (new - old) * sign
+            diff = q * (s0 - we) if int(e) == int(eid) else -we * q
+            p2[pos[e]] = we / s0 + diff
+            rhs[v] += d * x[u] * diff * sign
         tau = 1e-13 * np.abs(rhs).sum()
         r = fixed_point(g, d, x0=np.zeros(g.n), floor_tau=tau, patience=5, normalize=False,
                         csc_p=p2, rhs=rhs)
         total += r.x
-    return float(np.dot(grad_x, total) / (2.0 * h))
+        solve_err += d / (1.0 - d) * r.err
+    fd = float(np.dot(grad_x, total) / (2.0 * h))
+    if with_bound:
+        return fd, float(np.abs(grad_x).max() * solve_err / (2.0 * h))
+    return fd
 
 
-def fd_damping(g: Graph, x, grad_x, h=1e-6, d=0.85, csc_p=None):
+def fd_damping(g: Graph, x, grad_x, h=1e-6, d=0.85, csc_p=None, with_bound=False):
     """Central difference of L w.r.t. d with the same direct difference solves:
       (I - (d+h) M)(x+ - x) = h (M x - 1/n),  (I - (d-h) M)(x - x-) = h (M x - 1/n)."""
     n = g.n
@@ -378,8 +390,13 @@ def fd_damping(g: Graph, x, grad_x, h=1e-6, d=0.85, csc_p=None):
     rhs = h * (mx - 1.0 / n)
     tau = 1e-13 * np.abs(rhs).sum()
     total = np.zeros(n)
+    solve_err = 0.0
     for dd in (d + h, d - h):
         r = fixed_point(g, dd, x0=np.zeros(n), floor_tau=tau, patience=5, normalize=False,
                         csc_p=csc_p, rhs=rhs)
         total += r.x
-    return float(np.dot(grad_x, total) / (2.0 * h))
+        solve_err += dd / (1.0 - dd) * r.err
+    fd = float(np.dot(grad_x, total) / (2.0 * h))
+    if with_bound:
+        return fd, float(np.abs(grad_x).max() * solve_err / (2.0 * h))
+    return fd

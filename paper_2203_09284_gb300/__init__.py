@@ -44,7 +44,7 @@ class PrTune(ctypes.Structure):
     _fields_ = [("t_lo", ctypes.c_int32), ("t_hub", ctypes.c_int32), ("hub_seg", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("deterministic_gs", ctypes.c_int32),
                 ("stage_kb", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
-                ("test_stall", ctypes.c_int32), ("fused_split", ctypes.c_int32)]
+                ("fused_split", ctypes.c_int32)]
 
 
 class PrOptions(ctypes.Structure):
@@ -53,7 +53,8 @@ class PrOptions(ctypes.Structure):
                 ("precision", ctypes.c_int), ("norm", ctypes.c_int),
                 ("x0", ctypes.c_void_p), ("history", ctypes.c_void_p),
                 ("use_graph", ctypes.c_int32), ("max_outer", ctypes.c_int32),
-                ("inner_rel", ctypes.c_double), ("tune", ctypes.POINTER(PrTune))]
+                ("inner_rel", ctypes.c_double), ("tune", ctypes.POINTER(PrTune)),
+                ("no_rescale", ctypes.c_int32)]
 
 
 class PrResult(ctypes.Structure):
@@ -262,7 +263,7 @@ def pr_graph_export(handle, stream=None, csr=False):
 
 def make_options(d=0.85, threshold=1e-10, max_iter=1000, variant="jacobi", precision="fp64",
                  norm="l1", x0=None, history=None, use_graph=True, max_outer=0, inner_rel=0.0,
-                 tune=None):
+                 tune=None, no_rescale=False):
     o = pr_options_default()
     o.d, o.threshold, o.max_iter = float(d), float(threshold), int(max_iter)
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
@@ -273,6 +274,7 @@ def make_options(d=0.85, threshold=1e-10, max_iter=1000, variant="jacobi", preci
     o.use_graph = 1 if use_graph else 0
     o.max_outer = int(max_outer)
     o.inner_rel = float(inner_rel)
+    o.no_rescale = 1 if no_rescale else 0
     if tune is not None:
         t = tune if isinstance(tune, PrTune) else PrTune(**tune)
         o._tune_ref = t

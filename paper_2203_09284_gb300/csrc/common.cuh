@@ -125,7 +125,8 @@ struct Items {
     int32_t stage_kb = 0;         // shared-memory copy of the hottest sources
                                   // (KB; <= 0: none)
     int32_t wait_limit = 0;       // copy-barrier polls before a timeout (0: default)
-    int32_t test_stall = 0;       // testing only: force the timeout path
+    int32_t test_stall = 0;       // testing only (FUSEDPR_TEST_STALL): force the
+                                  // timeout path
     int32_t fused_split = 0;      // fused sweep launches (pr_tune.fused_split)
     Buf hubseg_start;             // [nhub + 1] first segment of each hub
     Buf seg_acc;                  // [nhubseg] double partial sums
@@ -202,6 +203,7 @@ void buf_free(pr_graph *g, Buf &b, cudaStream_t s);
 pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s);
 pr_status ensure_csr(pr_graph *g, cudaStream_t s);
 pr_tune effective_tune(const pr_graph *g, const pr_tune *t);
+int test_stall_requested();
 void release_graphs(pr_graph *g);
 
 // exclusive scan of `count` int32 values; out[count] receives the total.

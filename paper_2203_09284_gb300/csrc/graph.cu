@@ -11,6 +11,7 @@
 //      largest first; each in-list copied with its sources renamed
 //   5. work items: hub segments over [0, nhub), mid sub-ranges, low tiles
 //   6. (on demand) out-lists; (weighted graphs) row sums and P per slot
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -226,7 +227,6 @@ pr_tune effective_tune(const pr_graph *g, const pr_tune *t)
         if (t->stage_kb != 0) r.stage_kb = t->stage_kb;
         r.deterministic_gs = t->deterministic_gs;
         r.wait_limit = t->wait_limit > 0 ? t->wait_limit : 0;
-        r.test_stall = t->test_stall ? 1 : 0;
         r.fused_split = t->fused_split;
     }
     r.fused_split = std::max(0, std::min(r.fused_split, 2));
@@ -238,6 +238,16 @@ pr_tune effective_tune(const pr_graph *g, const pr_tune *t)
     r.hub_seg = std::max(256, std::min(r.hub_seg, 8192));
     r.tile = std::max(32, std::min(r.tile, 512));
     return r;
+}
+
+// Fault-injection hook for the tests of the bounded device waits (not part
+// of the C ABI): with FUSEDPR_TEST_STALL=1 in the environment, every sweep
+// block's first wait also waits on a barrier nothing arrives at, so the wait
+// runs out and the solve returns PR_ERR_TIMEOUT with the device still usable.
+int test_stall_requested()
+{
+    const char *v = getenv("FUSEDPR_TEST_STALL");
+    return (v && v[0] == '1') ? 1 : 0;
 }
 
 static void drop_temp(pr_graph *g, Buf &b, cudaStream_t s)
@@ -275,7 +285,7 @@ pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
     Items &it = g->items;
     it.stage_kb = t.stage_kb;
     it.wait_limit = t.wait_limit;
-    it.test_stall = t.test_stall;
+    it.test_stall = test_stall_requested();
     it.fused_split = t.fused_split;
     if (it.t_lo == t.t_lo && it.t_hub == t.t_hub && it.hub_seg == t.hub_seg &&
         it.tile_c == t.tile)
@@ -710,7 +720,6 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
     g->tune.deterministic_gs = 0;
     g->tune.stage_kb = 64;
     g->tune.wait_limit = 0;
-    g->tune.test_stall = 0;
     pr_status st = PR_OK;
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess)

@@ -343,7 +343,7 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
         p.inv = g->inv64.p;
         n2o = o2n = nullptr;
     }
-    p.renorm = gs ? 1 : 0;
+    p.renorm = (gs && !o->no_rescale) ? 1 : 0;
     SweepPlan plan;
     if (serial) {
         plan.func = reinterpret_cast<const void *>(&k_sweep_serial<T, A>);
@@ -366,7 +366,7 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
     bool graph_loop = false;
     if (o->use_graph) {
         const int key = (fp64 ? 1 : 0) | (gs ? 2 : 0) | (serial ? 4 : 0) | (weighted ? 8 : 0) |
-                        (g->items.test_stall ? 32 : 0);
+                        (g->items.test_stall ? 32 : 0) | (p.renorm ? 128 : 0);
         cudaGraphExec_t exec;
         PR_TRY(loop_graph(g, key, plan, &exec));
         PR_CUDA(cudaGraphLaunch(exec, s));
@@ -402,7 +402,7 @@ pr_status prepare_solve(pr_graph *g, const pr_options *o, pr_tune &tn, cudaStrea
     const Items &it = g->items;
     if (it.t_lo != tn.t_lo || it.t_hub != tn.t_hub || it.hub_seg != tn.hub_seg ||
         it.tile_c != tn.tile || it.stage_kb != tn.stage_kb || it.wait_limit != tn.wait_limit ||
-        it.test_stall != tn.test_stall || it.fused_split != tn.fused_split)
+        it.test_stall != test_stall_requested() || it.fused_split != tn.fused_split)
         release_graphs(g);  // cached loops hold the old launch parameters
     PR_TRY(ensure_items(g, tn, s));
     PR_TRY(ensure_workspace(g, s));

@@ -93,22 +93,59 @@ def test_pagerank_fn_autograd():
     assert abs(float(d.grad) - gd_ref) <= 1e-8 * abs(gd_ref)
 
 
-def test_backward_full_size_s18_sampled():
-    """R-MAT scale 18 with weights, 1,000 loss targets: FP32 adjoint and
-    gradients against FP64 central differences on sampled edges."""
+def test_backward_full_size_s18():
+    """R-MAT scale 18, raw weights uniform in (0, 1], 1,000 loss targets with
+    coefficients U(-1, 1) (the differentiable workload):
+      - the FP64 adjoint's edge-weight gradient against the oracle's adjoint
+        and gradients, edge by edge, to relative 1e-6 (floor 1e-12 of the
+        largest), and dL/dd likewise;
+      - the FP32 adjoint against the same, to 1e-5 of the largest gradient
+        (and in relative L2);
+      - the FP64 gradient against cancellation-free FP64 central differences
+        (h = 1e-6) of the oracle's fixed point on 100 sampled edges and d,
+        each to relative 1e-6 plus the solves' own error bound, and to
+        relative 1e-6 in L2 over the 100 edges.
+    The central differences (two oracle solves each) run in spawned host
+    processes while the GPU works."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+
+    import oracle_pool
     n, src, dst = gen.rmat(18, 16, seed=18)
     w = gen.edge_weights(len(src), seed=18)
     og = oracle.build_graph(n, src, dst)
     gx = _loss_grad(n, 18, 1000)
-    g = graph(n, src, dst, w=w)
-    xg, _ = g.solve(threshold=1e-14, max_iter=2000)
-    gw64, gd64, _ = g.backward(xg, dev(gx), threshold=1e-15, max_iter=5000)
-    gw32, gd32, _ = g.backward(xg, dev(gx), precision="fp32", threshold=1e-9, max_iter=2000)
-    a, b = gw64.cpu().numpy(), gw32.cpu().numpy()
-    assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
-    x = xg.cpu().numpy()
-    _, _, csc_p = oracle.row_normalize(og, w)
-    for e in gen.fd_edges(5, len(src), seed=18):
-        fd = oracle.fd_weight(og, w, x, gx, int(e), h=1e-6, d=D, csc_p=csc_p)
-        assert abs(a[e] - fd) <= 1e-6 * np.abs(a).max() + 1e-6 * abs(fd), (e, a[e], fd)
-    g.close()
+    s_, csr_p, csc_p = oracle.row_normalize(og, w)
+    xstar = oracle.fixed_point(og, D, csc_p=csc_p).x
+    lam, _, _ = oracle.adjoint(og, gx, D, csr_p=csr_p)
+    gw_ref, gd_ref = oracle.gradients(og, xstar, lam, D, w=w)
+    edges = [int(e) for e in gen.fd_edges(100, len(src), seed=18)]
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"),
+                                initializer=oracle_pool.init_weighted,
+                                initargs=(18, 16, 18, 18, xstar, gx, D)) as pool:
+        fut_e = [pool.submit(oracle_pool.fd_edge, e) for e in edges]
+        fut_d = pool.submit(oracle_pool.fd_damping)
+        g = graph(n, src, dst, w=w)
+        xg, _ = g.solve(threshold=1e-14, max_iter=2000)
+        gw64, gd64, r64 = g.backward(xg, dev(gx), threshold=1e-15, max_iter=5000)
+        gw32, gd32, r32 = g.backward(xg, dev(gx), precision="fp32", threshold=1e-9,
+                                     max_iter=2000)
+        g.close()
+        a, b = gw64.cpu().numpy(), gw32.cpu().numpy()
+        scale = np.abs(gw_ref).max()
+        bad = np.abs(a - gw_ref) > 1e-6 * np.abs(gw_ref) + 1e-12 * scale
+        assert not bad.any(), (int(bad.sum()), np.abs(a - gw_ref)[bad][:5], gw_ref[bad][:5])
+        assert abs(float(gd64) - gd_ref) <= 1e-6 * abs(gd_ref)
+        assert np.abs(b - gw_ref).max() <= 1e-5 * scale
+        assert np.linalg.norm(b - gw_ref) <= 1e-5 * np.linalg.norm(gw_ref)
+        assert abs(float(gd32) - gd_ref) <= 1e-5 * abs(gd_ref)
+        fd = np.array([f.result()[0] for f in fut_e])
+        noise = np.array([f.result()[1] for f in fut_e])
+        fdd, noise_d = fut_d.result()
+    ae = a[edges]
+    bad = np.abs(ae - fd) > 1e-6 * np.abs(fd) + noise + 1e-12 * np.abs(fd).max()
+    assert not bad.any(), list(zip(np.array(edges)[bad], ae[bad], fd[bad], noise[bad]))
+    assert np.linalg.norm(ae - fd) <= 1e-6 * np.linalg.norm(fd)
+    assert abs(float(gd64) - fdd) <= 1e-6 * abs(fdd) + noise_d

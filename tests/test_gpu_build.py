@@ -34,6 +34,14 @@ def check_build(n, src, dst, t_lo=32, t_hub=4096):
     info = g.info()
     assert info["n_dangling"] == int((o.outdeg == 0).sum())
     assert info["bins"] == [len(low), len(mid), len(hub)]
+    # bin membership: the classes are contiguous ranges of the degree-ordered
+    # ids (hubs first, then mid, then low), so each bin's input ids, sorted,
+    # are the oracle's bin list
+    nh, nm = len(hub), len(mid)
+    n2o_g = c("new_to_old")
+    assert np.array_equal(np.sort(n2o_g[:nh]), hub)
+    assert np.array_equal(np.sort(n2o_g[nh:nh + nm]), mid)
+    assert np.array_equal(np.sort(n2o_g[nh + nm:]), low)
     g.close()
 
 

@@ -161,6 +161,61 @@ def test_jacobi_trajectory_is_exact_to_rounding():
         assert np.max(np.abs(r.x - exact) / exact) < 1e-14
 
 
+def _exact_fused(n, src, dst, d, sweeps, rescale):
+    """Eq. 9 in exact rationals: vertices in increasing id order, each in-list
+    sum reading the contributions as they stand (already rewritten for
+    in-neighbours j < i, old for j >= i), dangling mass D taken at the start of
+    the sweep and spread uniformly; with rescale, each sweep ends with x /= sum
+    x.  Returns the iterate and each sweep's L1 change (new value against the
+    value it replaced, before any rescale)."""
+    outdeg = np.bincount(src, minlength=n)
+    ins = [[int(v) for v, t in zip(src, dst) if t == u] for u in range(n)]
+    x = [Fraction(1, n)] * n
+    c = [x[v] / int(outdeg[v]) if outdeg[v] else Fraction(0) for v in range(n)]
+    errs = []
+    for _ in range(sweeps):
+        dang = sum(x[u] for u in range(n) if outdeg[u] == 0)
+        err = Fraction(0)
+        for u in range(n):
+            new = (1 - d) / n + d * (sum(c[v] for v in ins[u]) + dang / n)
+            err += abs(new - x[u])
+            x[u] = new
+            c[u] = new / int(outdeg[u]) if outdeg[u] else Fraction(0)
+        errs.append(err)
+        if rescale:
+            s = sum(x)
+            x = [v / s for v in x]
+            c = [x[v] / int(outdeg[v]) if outdeg[v] else Fraction(0) for v in range(n)]
+    return x, errs
+
+
+@pytest.mark.parametrize("rescale", [False, True])
+@pytest.mark.parametrize("seed", [3, 12])
+def test_fused_trajectory_is_exact_to_rounding(seed, rescale):
+    """The oracle's sequential fused sweep, with and without the per-sweep
+    rescale to sum 1, against exact rationals after 1-4 sweeps on small graphs
+    with dangling vertices (where the rescale and the dangling term matter)
+    and a self-loop (Eq. 9 reads its own old value)."""
+    n, src, dst = gen.random_digraph(7, 0.3, seed=seed, self_loops=True)
+    outdeg = np.bincount(src, minlength=n)
+    assert (outdeg == 0).any() and (src == dst).any()
+    g = oracle.build_graph(n, src, dst)
+    for k in range(1, 5):
+        x, errs = _exact_fused(n, src, dst, Fraction(17, 20), k, rescale)
+        r = oracle.gauss_seidel(g, 0.85, tau=-1, max_iter=k, normalize=False, renorm=rescale)
+        exact = np.array([float(v) for v in x])
+        assert np.max(np.abs(r.x - exact) / exact) < 1e-14, k
+        want = np.array([float(e) for e in errs])
+        assert np.allclose(r.history, want, rtol=1e-13, atol=0), k
+    # without the rescale the sum drifts (dangling mass read at sweep start,
+    # in-neighbours read partly updated values); with it the sum stays 1
+    x, _ = _exact_fused(n, src, dst, Fraction(17, 20), 3, rescale)
+    if rescale:
+        assert sum(x) == 1
+    else:
+        assert sum(x) != 1
+
+
 # --- invariants and agreement between variants -----------------------------
 
 @pytest.mark.parametrize("seed", [1, 2])
