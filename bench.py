@@ -174,8 +174,10 @@ def measure_rows(dev, stream, peak, timed):
     g = fp.Graph(n, torch.from_numpy(s_h).to(dev), torch.from_numpy(d_h).to(dev))
     seeds = torch.from_numpy(gen.seed_vertices(256, n, seed=1)).to(dev)
     row = {"workload": "rmat20_ef16_seed4_B256_onehot", "n": n, "edges": m, "threshold": 1e-8}
+    Xs = {}
     for prec in ("fp32", "fp64"):
         ms, (X, res) = timed(lambda: g.solve_batched(seeds, threshold=1e-8, precision=prec), 2)
+        Xs[prec] = (X.double(), [i for i, r in enumerate(res) if r.status != 0])
         t1, _ = timed(lambda: g.solve_batched(seeds, threshold=0.0, max_iter=1, precision=prec), 2)
         t9, _ = timed(lambda: g.solve_batched(seeds, threshold=0.0, max_iter=9, precision=prec), 2)
         sweep_ms = (t9 - t1) / 8
@@ -189,6 +191,13 @@ def measure_rows(dev, stream, peak, timed):
                      "row_gather_GBps": round(gathered / (sweep_ms * 1e-3) / 1e9, 1),
                      "frac_of_hbm": round(gathered / (sweep_ms * 1e-3) / 1e9 / peak, 3),
                      "teps_x_columns_G": round(m * 256 * sweeps / (ms * 1e-3) / 1e9, 1)}
+    # accuracy of the FP32 columns: L1 distance to the FP64 columns (both
+    # stopped at 1e-8, so each is within ~5.7e-8 of its fixed point)
+    col_l1 = (Xs["fp32"][0] - Xs["fp64"][0]).abs().sum(dim=0).cpu()
+    row["fp32_vs_fp64_col_l1"] = {"max": float(col_l1.max()), "median": float(col_l1.median()),
+                                  "not_converged_fp32": Xs["fp32"][1],
+                                  "not_converged_fp64": Xs["fp64"][1]}
+    del Xs
     ms64, _ = timed(lambda: g.solve(threshold=1e-8), 2)
     row["single_vector_fp64_ms"] = round(ms64, 3)
     g.close()
@@ -203,6 +212,7 @@ def measure_rows(dev, stream, peak, timed):
         graphs.append(fp.Graph(nn, torch.from_numpy(ss).to(dev), torch.from_numpy(dd).to(dev)))
     row = {"workload": "64 rmat graphs, scale 10-18, ef 8-32, seed 1", "edges": E}
     from paper_2203_09284_gb300 import tune
+    xs_by = {}
     for prec, thr in (("fp64", 1e-10), ("fp32", 1e-6)):
         best, _ = tune.autotune_multi(graphs, precision=prec, sweeps=3)  # not timed
         ms, (xs, res) = timed(lambda: fp.solve_multi(graphs, threshold=thr, precision=prec,
@@ -216,8 +226,15 @@ def measure_rows(dev, stream, peak, timed):
                      "tune": best,
                      "max_sweeps": max(r.iters for r in res),
                      "gteps": round(sum(r.iters * gg.m for r, gg in zip(res, graphs))
-                                    / (ms * 1e-3) / 1e9, 1)}
+                                    / (ms * 1e-3) / 1e9, 1),
+                     "not_converged": [i for i, r in enumerate(res) if r.status != 0]}
+        xs_by[prec] = [x.clone() for x in xs]
         del sweeps
+    # accuracy of the FP32 results (stopped at an L1 change of 1e-6, near
+    # FP32's rounding floor on the larger graphs): L1 distance to the FP64 ones
+    row["fp32"]["max_l1_vs_fp64"] = max(float((a - b).abs().sum())
+                                        for a, b in zip(xs_by["fp32"], xs_by["fp64"]))
+    del xs_by
     for gg in graphs:
         gg.close()
     rows["multi_graph"] = row
@@ -232,11 +249,18 @@ def measure_rows(dev, stream, peak, timed):
     gx[t_] = c_
     gx = torch.from_numpy(gx).to(dev)
     row = {"workload": "rmat18_ef16_seed18_weighted_1000targets", "n": n, "edges": len(s_h)}
-    for prec, thr in (("fp64", 1e-12), ("fp32", 1e-8)):
+    gw_ref, gd_ref, _ = g.backward(xg, gx, precision="fp64", threshold=1e-15, max_iter=5000)
+    ref_norm = float(gw_ref.norm())
+    # each form's time next to its gradient error (relative L2 over all edge
+    # weights, and of dL/dd) against an FP64 backward to an L1 change of 1e-15
+    for key, prec, thr in (("fp64", "fp64", 1e-12), ("fp64_1e-8", "fp64", 1e-8),
+                           ("fp32", "fp32", 1e-8)):
         ms, (gw, gd, r) = timed(lambda: g.backward(xg, gx, precision=prec, threshold=thr), 2)
         fms, (_, fr) = timed(lambda: g.solve(threshold=thr, precision=prec), 2)
-        row[prec] = {"threshold": thr, "backward_ms": round(ms, 3), "adjoint_sweeps": r.iters,
-                     "forward_ms": round(fms, 3), "forward_sweeps": fr.iters}
+        row[key] = {"threshold": thr, "backward_ms": round(ms, 3), "adjoint_sweeps": r.iters,
+                    "forward_ms": round(fms, 3), "forward_sweeps": fr.iters,
+                    "grad_w_rel_l2_err": float((gw - gw_ref).norm()) / ref_norm,
+                    "grad_d_rel_err": abs(float(gd) - float(gd_ref)) / abs(float(gd_ref))}
     g.close()
     rows["adjoint"] = row
 
@@ -251,11 +275,16 @@ def measure_rows(dev, stream, peak, timed):
     x = torch.empty(n, dtype=torch.float64, device=dev)
     row = {"workload": "rmat25_ef16_seed1", "n": n, "edges": m, "threshold": 1e-10,
            "build_ms": round(build_ms, 2)}
+    x_ref, _ = g.solve(variant="jacobi", precision="fp64", threshold=1e-13, max_iter=2000)
     for prec in ("fp64", "fp32_dc", "bf16_dc", "fp16_dc"):
         ms, (_, r) = timed(lambda: g.solve(out=x, variant="jacobi", precision=prec,
                                            threshold=1e-10, max_iter=1000), 2)
         row[prec] = {"ms": round(ms, 2), "iters": r.iters, "outer": r.outer_iters,
-                     "residual": r.residual, "status": r.status}
+                     "residual": r.residual, "status": r.status,
+                     "l1_vs_fp64_1e-13": float((x - x_ref).abs().sum())}
+    for prec in ("fp32_dc", "bf16_dc", "fp16_dc"):
+        row[prec]["speedup_vs_fp64"] = round(row["fp64"]["ms"] / row[prec]["ms"], 3)
+    del x_ref
     g.close()
     del x
     torch.cuda.empty_cache()
@@ -313,6 +342,9 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     ms_total = ev0.elapsed_time(ev1)
     launches = fp.kernel_launches() - launches0
+    bad = [(i, r.status) for i, rs in enumerate(all_res) for r in rs if r.status != fp.PR_OK]
+    if bad:
+        raise RuntimeError(f"a timed solve did not converge (step, status): {bad}")
     ms_step = max_over_ranks(ms_total, world, dev) / args.steps
     sweeps = sum(r.iters + r.outer_iters for r in all_res[-1])
     value = world * m * sweeps / (ms_step * 1e-3) / 1e9
@@ -332,18 +364,26 @@ def run_ours(args, rank, world):
         return best, out
 
     build_ms, g = timed(lambda: fp.Graph(n, src, dst))
+    # accuracy reference: FP64 Jacobi to an L1 change of 1e-13 (within
+    # d/(1-d) * 1e-13 = 5.7e-13 of the fixed point)
+    x_ref, r_ref = g.solve(variant="jacobi", precision="fp64", threshold=1e-13, max_iter=2000)
+    if r_ref.status != fp.PR_OK:
+        raise RuntimeError("the FP64 reference solve did not converge")
     solves = {}
     for prec in dict.fromkeys([args.precision, "fp64"]):
         for v in variants:
             ms, (x, r) = timed(lambda: g.solve(out=x_out[0], variant=v, precision=prec,
                                                threshold=1e-10, max_iter=1000))
+            if r.status != fp.PR_OK:
+                raise RuntimeError(f"solve {v}/{prec} ended with status {r.status}")
             # algorithmic bytes of the solve: its sweeps in their own
             # precision and the FP64 residual sweeps of defect correction
             alg_solve = r.iters * b_alg(n, m, prec) + r.outer_iters * b_alg(n, m, "fp64")
             solves[f"{v}_{prec}"] = {"ms": round(ms, 4), "iters": r.iters,
                                      "outer": r.outer_iters, "residual": r.residual,
                                      "gteps": round(m * (r.iters + r.outer_iters) / ms / 1e6, 2),
-                                     "alg_GBps": round(alg_solve / (ms * 1e-3) / 1e9, 1)}
+                                     "alg_GBps": round(alg_solve / (ms * 1e-3) / 1e9, 1),
+                                     "l1_vs_fp64_1e-13": float((x - x_ref).abs().sum())}
 
     # dominant kernel: the cheap sweep of the headline precision, timed by
     # events around back-to-back launches of the device loop
@@ -362,6 +402,12 @@ def run_ours(args, rank, world):
     peak = peak or 6800.0
     for sv in solves.values():  # % of HBM peak per solve (the metric's definition)
         sv["hbm_frac"] = round(sv["alg_GBps"] / peak, 4)
+    # speedup of each form over the plain FP64 solve of the same sweep; all
+    # stop at the FP64 rule (L1 change or FP64 residual <= 1e-10), and each
+    # row's l1_vs_fp64_1e-13 gives its accuracy
+    for k, sv in solves.items():
+        v = k.split("_", 1)[0]
+        sv["speedup_vs_fp64"] = round(solves[f"{v}_fp64"]["ms"] / sv["ms"], 3)
     achieved = alg / (sweep_ms * 1e-3) / 1e9
     # the gathers alone (same index stream, same staging of the first 64 KB):
     # a measured ceiling for the irregular part of the sweep
@@ -439,6 +485,31 @@ def run_ours(args, rank, world):
     return out
 
 
+def host_info():
+    """The host the CPU numbers come from: usable cores, CPU model, machine."""
+    import platform
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            k = line.split(":", 1)[0].strip().lower()
+            if k in ("model name", "cpu model", "hardware"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return {"cores_available": len(os.sched_getaffinity(0)), "cpu_model": model,
+            "machine": platform.machine(), "threads_used": 1}
+
+
 def cpu_baseline(scale, budget_s=15.0):
     """The oracle (single-threaded FP64) on a bounded sample of the workload."""
     import oracle
@@ -456,7 +527,7 @@ def cpu_baseline(scale, budget_s=15.0):
         t += time.perf_counter() - t1
         sweeps += 4
     return {"value": round(m * sweeps / t / 1e9, 4), "unit": "GTEPS", "cores": 1,
-            "kind": "oracle",
+            "kind": "oracle", "host": host_info(),
             "sample": f"{sweeps} FP64 sweeps (half Jacobi, half fused) of the R-MAT-{scale} "
                       f"graph after an oracle build of {t_build:.1f} s; single thread"}
 
@@ -630,7 +701,7 @@ def reference_arm(args, world=1):
             "config": {"workload": f"rmat{args.scale}_ef16_dangling10_seed1", "n": n,
                        "edges": m, "precision": args.precision},
             "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": 1,
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "sample": sample, "host": host_info()},
             "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

@@ -66,6 +66,8 @@ def _load():
                   _I32, _F64, _F64, _F64]
             lib.orc_jacobi.argtypes = _PROBLEM + it
             lib.orc_gauss_seidel.argtypes = _PROBLEM + [ctypes.c_int32] + it
+            lib.orc_perforated.argtypes = _PROBLEM + [ctypes.c_double, ctypes.c_int32] + it + [
+                ctypes.POINTER(ctypes.c_int64)]
             lib.orc_fixed_point.argtypes = _PROBLEM + [_F64, ctypes.c_double, ctypes.c_int32,
                                                        ctypes.c_int32, ctypes.c_int32, _F64,
                                                        _I32, _F64, _F64]
@@ -221,6 +223,37 @@ def gauss_seidel(g: Graph, d=0.85, tau=1e-10, max_iter=200, norm=NORM_L1, normal
     sweep ends with x /= sum x (the sum drifts under in-place updates)."""
     return _iterate(_load().orc_gauss_seidel, g, d, tau, max_iter, norm, normalize, x0,
                     pre=(1 if renorm else 0,), **kw)
+
+
+@dataclass
+class PerforatedResult(Result):
+    gathered: int = 0
+
+
+def perforated(g: Graph, d=0.85, eps=1e-8, period=0, tau=1e-10, max_iter=200, norm=NORM_L1,
+               normalize=True, x0=None, **kw) -> PerforatedResult:
+    """Loop-perforated Jacobi: in a perforated sweep a vertex whose last
+    change was below eps times its value keeps it (no in-list sum).  With
+    period > 0 every period-th sweep is full and only those stop; with period
+    0 any sweep stops.  ``gathered`` = in-list entries summed in all sweeps."""
+    lib = _load()
+    args, keep = _problem(g, d, **kw)
+    x0 = _f64(x0)
+    x = np.empty(g.n, np.float64)
+    hist = np.zeros(max(max_iter, 1), np.float64)
+    iters = ctypes.c_int32(0)
+    err = ctypes.c_double(0)
+    sb = ctypes.c_double(0)
+    gathered = ctypes.c_int64(0)
+    rc = lib.orc_perforated(*args, float(eps), int(period), _p(x0, _F64), float(tau),
+                            int(max_iter), int(norm), 1 if normalize else 0, _p(x, _F64),
+                            ctypes.byref(iters), ctypes.byref(err), _p(hist, _F64),
+                            ctypes.byref(sb), ctypes.byref(gathered))
+    del keep
+    if rc not in (OK, NOT_CONVERGED):
+        raise ValueError(f"orc_perforated failed ({rc})")
+    return PerforatedResult(x, iters.value, err.value, hist[:iters.value].copy(), sb.value, rc,
+                            gathered.value)
 
 
 def fixed_point(g: Graph, d=0.85, x0=None, floor_tau=0.0, patience=5, max_iter=5000,

@@ -17,6 +17,10 @@
  *                    dangling-mass term added; L1 or max-norm stop (Eq. 3).
  *   orc_gauss_seidel Algorithm 2 (FusEd-PageRank), i.e. Eq. 9 taken in
  *                    increasing vertex id order.
+ *   orc_perforated   loop-perforated Jacobi (the loop perforation the paper
+ *                    names in its related work and future work): vertices
+ *                    of minor importance skip their in-list sums in some
+ *                    sweeps.
  *   orc_adjoint      transposed fixed point of the same operator.
  *   orc_gradients    chain rule of the fixed point w.r.t. raw edge weights
  *                    and the damping factor d.
@@ -403,6 +407,92 @@ int orc_gauss_seidel(PROBLEM_ARGS, int32_t renorm, const double *x0, double tau,
     MAKE_PROBLEM;
     return run_iteration(&p, 1, renorm, x0, tau, max_iter, norm, normalize, x_out, iters,
                          err_last, err_hist, sum_before);
+}
+
+/*
+ * Loop-perforated Jacobi.  The paper names loop perforation (related work:
+ * skipping the computations on vertices of minor importance, an approximate
+ * computing technique; conclusion: future work) without defining it; the
+ * reading implemented here:
+ *   - a vertex whose change at its last computation was below eps times its
+ *     current value (|x_new - x_old| < eps * x) has (nearly) stopped moving:
+ *     in a perforated sweep it keeps its value and its in-list is not summed;
+ *     every other vertex takes the Jacobi update of Algorithm 1 (the dangling
+ *     mass D and the contributions come from the whole iterate at the start
+ *     of the sweep, as in orc_jacobi);
+ *   - with period > 0, sweep k (k = 0, 1, ...) is a full Jacobi sweep when k
+ *     is a multiple of period, and only a full sweep can stop the iteration;
+ *     with period 0 every sweep but the first is perforated and any sweep can
+ *     stop (the approximate-computing form: the error of a sweep counts the
+ *     vertices it computed, a skipped vertex changes by 0);
+ *   - the stop rule is Algorithm 1's, and the result is normalised at the end.
+ * Before its first computation a vertex has an infinite last change, so the
+ * first sweep is always full; eps 0 or period 1 is plain Jacobi.  *gathered
+ * receives the number of in-list entries summed over all sweeps.
+ */
+int orc_perforated(PROBLEM_ARGS, double eps, int32_t period, const double *x0, double tau,
+                   int32_t max_iter, int32_t norm, int32_t normalize, double *x_out,
+                   int32_t *iters, double *err_last, double *err_hist, double *sum_before,
+                   int64_t *gathered)
+{
+    MAKE_PROBLEM;
+    if (n < 1 || max_iter < 0 || period < 0 || !(eps >= 0.0)) return ORC_ERR_ARG;
+    double *x = x_out;
+    double *xn = (double *)malloc(sizeof(double) * (size_t)n);
+    double *c = (double *)malloc(sizeof(double) * (size_t)n);
+    double *last = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!xn || !c || !last) { free(xn); free(c); free(last); return ORC_ERR_OOM; }
+    for (int32_t u = 0; u < n; ++u) {
+        x[u] = x0 ? x0[u] : 1.0 / (double)n;
+        last[u] = INFINITY;
+    }
+    const double base = (1.0 - p.d) / (double)n;
+    const double inv_n = 1.0 / (double)n;
+    int64_t edges = 0;
+    int32_t k = 0;
+    double err = INFINITY;
+    int converged = 0;
+    while (k < max_iter) {
+        const int full = period > 0 && (k % period) == 0;
+        const double D = dangling_mass(&p, x);
+        if (!p.csc_p)
+            for (int32_t v = 0; v < n; ++v) c[v] = x[v] * p.inv_outdeg[v];
+        ksum l1 = {0.0, 0.0};
+        double mx = 0.0;
+        for (int32_t u = 0; u < n; ++u) {
+            if (!full && last[u] < eps * x[u]) {
+                xn[u] = x[u];
+                continue;
+            }
+            double sum = 0.0;
+            for (int32_t q = p.col_ptr[u]; q < p.col_ptr[u + 1]; ++q) {
+                int32_t v = p.row_idx[q];
+                sum += p.csc_p ? p.csc_p[q] * x[v] : c[v];
+            }
+            edges += p.col_ptr[u + 1] - p.col_ptr[u];
+            xn[u] = r_of(&p, u, base) + p.d * (sum + D * w_of(&p, u, inv_n));
+            const double diff = fabs(xn[u] - x[u]);
+            last[u] = diff;
+            ks_add(&l1, diff);
+            if (diff > mx) mx = diff;
+        }
+        memcpy(x, xn, sizeof(double) * (size_t)n);
+        err = norm == 0 ? ks_get(&l1) : mx;
+        if (err_hist) err_hist[k] = err;
+        ++k;
+        if ((full || period == 0) && err <= tau) { converged = 1; break; }
+    }
+    const double s = total(x, n);
+    if (sum_before) *sum_before = s;
+    if (normalize)
+        for (int32_t u = 0; u < n; ++u) x[u] = x[u] / s;
+    *iters = k;
+    *err_last = err;
+    if (gathered) *gathered = edges;
+    free(xn);
+    free(c);
+    free(last);
+    return converged ? ORC_OK : ORC_NOT_CONVERGED;
 }
 
 /*

@@ -290,3 +290,90 @@ def test_ppr_with_dangling_matches_dense():
                           normalize=False)
         dense = oracle.dense_pagerank(n, src, dst, D, tele=v, dangling_along_tele=along)
         assert np.abs(r.x - dense).sum() < 1e-13
+
+
+# --- loop perforation -------------------------------------------------------
+
+def _exact_perforated(n, src, dst, d, eps, period, sweeps):
+    """The perforation rule in exact rationals: in a perforated sweep a vertex
+    whose change at its last computation was below eps times its value keeps
+    that value; every period-th sweep (and the first) is a full Jacobi
+    sweep.  Returns the iterates, the per-sweep L1 changes and the skip sets."""
+    outdeg = np.bincount(src, minlength=n)
+    ins = [[int(v) for v, t in zip(src, dst) if t == u] for u in range(n)]
+    x = [Fraction(1, n)] * n
+    last = [None] * n  # None: never computed (infinite)
+    errs, skips, margins = [], [], []
+    for k in range(sweeps):
+        full = (period > 0 and k % period == 0) or k == 0
+        dang = sum(x[u] for u in range(n) if outdeg[u] == 0)
+        c = [x[v] / int(outdeg[v]) if outdeg[v] else Fraction(0) for v in range(n)]
+        new, skip, err = list(x), set(), Fraction(0)
+        for u in range(n):
+            if not full and last[u] is not None:
+                margins.append(abs(last[u] - eps * x[u]) / (eps * x[u]))
+                if last[u] < eps * x[u]:
+                    skip.add(u)
+                    continue
+            new[u] = (1 - d) / n + d * (sum(c[v] for v in ins[u]) + dang / n)
+            last[u] = abs(new[u] - x[u])
+            err += last[u]
+        x = new
+        errs.append(err)
+        skips.append(skip)
+    return x, errs, skips, margins
+
+
+def test_perforated_is_jacobi_without_skips():
+    n, src, dst = gen.rmat(10, 8, seed=3, dangling_frac=0.2)
+    g = oracle.build_graph(n, src, dst)
+    ja = oracle.jacobi(g, D, tau=1e-12, max_iter=500)
+    for eps, period in ((0.0, 0), (1e-3, 1)):
+        r = oracle.perforated(g, D, eps=eps, period=period, tau=1e-12, max_iter=500)
+        assert r.iters == ja.iters and np.array_equal(r.x, ja.x)
+        assert np.array_equal(r.history, ja.history)
+        assert r.gathered == ja.iters * g.m
+    # no skips, but only every third sweep may stop: the same sweeps,
+    # continued to the next full one
+    r = oracle.perforated(g, D, eps=0.0, period=3, tau=1e-12, max_iter=500)
+    assert r.iters == ja.iters + (-(ja.iters - 1)) % 3 and (r.iters - 1) % 3 == 0
+    assert np.array_equal(r.history[:ja.iters], ja.history)
+    assert r.gathered == r.iters * g.m
+
+
+@pytest.mark.parametrize("period", [0, 3])
+def test_perforated_trajectory_is_exact_to_rounding(period):
+    """Iterates, per-sweep changes and the number of gathered in-list entries
+    against the rule in exact rationals; eps is chosen so that vertices are
+    skipped (and no skip decision lies within rounding of the threshold)."""
+    n, src, dst = gen.random_digraph(8, 0.3, seed=7)
+    g = oracle.build_graph(n, src, dst)
+    eps = Fraction(1, 20)
+    indeg = np.bincount(dst, minlength=n)
+    x, errs, skips, margins = _exact_perforated(n, src, dst, Fraction(17, 20), eps, period, 9)
+    assert sum(len(s) for s in skips) >= 5 and min(margins) > 1e-9
+    for k in range(1, 10):
+        r = oracle.perforated(g, 0.85, eps=float(eps), period=period, tau=-1, max_iter=k,
+                              normalize=False)
+        xk, ek, sk, _ = _exact_perforated(n, src, dst, Fraction(17, 20), eps, period, k)
+        exact = np.array([float(v) for v in xk])
+        assert np.max(np.abs(r.x - exact) / exact) < 1e-14, k
+        assert np.allclose(r.history, [float(e) for e in ek], rtol=1e-13, atol=0), k
+        assert r.gathered == sum(int(indeg.sum()) - int(indeg[list(s)].sum()) for s in sk), k
+
+
+def test_perforated_full_sweep_stop_certifies_the_bound():
+    """With period > 0 the iteration stops only after a full Jacobi sweep, so
+    the stop rule's a-posteriori bound d/(1-d) tau holds; with period 0 the
+    result is approximate (the skipped vertices' changes are not counted)
+    and fewer in-list entries are summed."""
+    n, src, dst = gen.rmat(12, 16, seed=2, dangling_frac=0.1)
+    g = oracle.build_graph(n, src, dst)
+    star = oracle.fixed_point(g, D)
+    ja = oracle.jacobi(g, D, tau=1e-10, max_iter=500)
+    for eps in (1e-9, 1e-7):
+        r = oracle.perforated(g, D, eps=eps, period=4, tau=1e-10, max_iter=2000)
+        assert r.status == oracle.OK and (r.iters - 1) % 4 == 0
+        assert np.abs(r.x - star.x).sum() <= D / (1 - D) * 1e-10
+        a = oracle.perforated(g, D, eps=eps, period=0, tau=1e-10, max_iter=2000)
+        assert a.status == oracle.OK and a.gathered < ja.iters * g.m
