@@ -140,6 +140,20 @@ typedef struct {
                                is still normalised once at the end); 0
                                (default) rescales.  Ignored by Jacobi and the
                                *_DC forms. */
+    double perforate_eps;   /* > 0: loop-perforated Jacobi (the loop perforation
+                               the paper's related work and conclusion name;
+                               PR_JACOBI, PR_FP64 / PR_FP32, unweighted): in a
+                               perforated sweep a vertex whose change at its
+                               last computation was below perforate_eps times
+                               its value keeps that value and its in-edges are
+                               not gathered.  0 (default): plain Jacobi. */
+    int32_t perforate_period; /* with perforate_eps > 0: sweep k (from 0) is a
+                               full Jacobi sweep when k == 0 or k is a multiple
+                               of perforate_period, and only full sweeps can
+                               stop (the stop rule's bound then holds); 0: no
+                               forced full sweeps, any sweep can stop (an
+                               approximate result: skipped vertices count as
+                               unchanged in the error). */
 } pr_options;
 
 typedef struct {
@@ -148,6 +162,9 @@ typedef struct {
     double residual;        /* final stop value */
     double sum_before_norm; /* sum of the iterate before the final x /= sum */
     pr_status status;
+    int64_t gathered;       /* pr_solve: in-list entries summed by its sweeps
+                               (inner, and FP64 residual sweeps for *_DC;
+                               fewer than sweeps x m when perforated) */
 } pr_result;
 
 /* Fills `o` with the defaults: d 0.85, threshold 1e-10, max_iter 1000,

@@ -54,13 +54,14 @@ class PrOptions(ctypes.Structure):
                 ("x0", ctypes.c_void_p), ("history", ctypes.c_void_p),
                 ("use_graph", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("inner_rel", ctypes.c_double), ("tune", ctypes.POINTER(PrTune)),
-                ("no_rescale", ctypes.c_int32)]
+                ("no_rescale", ctypes.c_int32), ("perforate_eps", ctypes.c_double),
+                ("perforate_period", ctypes.c_int32)]
 
 
 class PrResult(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("outer_iters", ctypes.c_int32),
                 ("residual", ctypes.c_double), ("sum_before_norm", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("gathered", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -263,7 +264,7 @@ def pr_graph_export(handle, stream=None, csr=False):
 
 def make_options(d=0.85, threshold=1e-10, max_iter=1000, variant="jacobi", precision="fp64",
                  norm="l1", x0=None, history=None, use_graph=True, max_outer=0, inner_rel=0.0,
-                 tune=None, no_rescale=False):
+                 tune=None, no_rescale=False, perforate_eps=0.0, perforate_period=0):
     o = pr_options_default()
     o.d, o.threshold, o.max_iter = float(d), float(threshold), int(max_iter)
     o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
@@ -275,6 +276,8 @@ def make_options(d=0.85, threshold=1e-10, max_iter=1000, variant="jacobi", preci
     o.max_outer = int(max_outer)
     o.inner_rel = float(inner_rel)
     o.no_rescale = 1 if no_rescale else 0
+    o.perforate_eps = float(perforate_eps)
+    o.perforate_period = int(perforate_period)
     if tune is not None:
         t = tune if isinstance(tune, PrTune) else PrTune(**tune)
         o._tune_ref = t

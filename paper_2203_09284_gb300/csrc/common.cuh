@@ -102,6 +102,13 @@ struct SolveState {
                         // (stored units), set by the sweep's last block
     unsigned int shift_ticket;  // blocks of the shift kernel done
     double *history;
+    // loop perforation (Jacobi): sweep k is full when k == 0 or
+    // (perf_period > 0 and k % perf_period == 0); a perforated sweep skips a
+    // vertex whose last change was below perf_eps times its value
+    int perf;                   // 1: perforated solve
+    int perf_period;
+    double perf_eps;
+    unsigned long long gathered;  // in-list entries summed (perforated solves)
 };
 
 // Work decomposition of a sweep in the degree-ordered ids (in-degree
@@ -171,6 +178,7 @@ struct pr_graph {
     fpr::Buf rbuf;      // n x 8 bytes: residual / right-hand side
     fpr::Buf state;     // SolveState
     fpr::Buf aux;       // scratch for batched / multi / adjoint
+    fpr::Buf lastbuf;   // perforated solves: last change per vertex
 
     // batched personalised PageRank: hub segments of the row gather
     // (vertices [0, bnhub) with more than BATCH_SEG in-edges), iterates and

@@ -369,7 +369,7 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     q.p.st = sx;
     q.r32 = g->rbuf.as<float>();
     SweepParams inner;
-    fill_params(g, inner, false, sizeof(Te), gs);  // correction buffers in ybuf, FP32 1/outdeg
+    fill_params(g, inner, false, sizeof(Te), false);  // correction buffers in ybuf, FP32 1/outdeg
     q.e0 = inner.y0;
     q.e1 = inner.y1;
     q.inv32 = g->r_inv32.as<float>();
@@ -471,6 +471,7 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
         res->residual = hs[0].norm ? hs[0].resmax : hs[0].res;
         res->sum_before_norm = hs[0].sigma * hs[0].sum;
         res->status = st;
+        res->gathered = (int64_t)hs[0].iter * g->m;
     }
     return st;
 }

@@ -42,6 +42,10 @@ pr_status validate_options(const pr_options *o)
         set_error("unknown norm");
         return PR_ERR_INVALID_ARG;
     }
+    if (!(o->perforate_eps >= 0.0) || std::isinf(o->perforate_eps) || o->perforate_period < 0) {
+        set_error("need perforate_eps >= 0 (finite) and perforate_period >= 0");
+        return PR_ERR_INVALID_ARG;
+    }
     return PR_OK;
 }
 
@@ -66,7 +70,7 @@ pr_status ensure_workspace(pr_graph *g, cudaStream_t s)
 // static shared memory of a sweep block (partial sums) plus slack
 constexpr int SWEEP_STATIC_SMEM = 2048;
 
-void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs)
+void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool perf)
 {
     Items &it = g->items;
     memset(&p, 0, sizeof(p));
@@ -88,7 +92,7 @@ void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs)
     // staged copy of stage_kb KB, at most the room left beside the warp
     // slices (shared memory is taken from the L1 cache, which also keeps hot
     // contributions, so a modest copy serves best)
-    const Layout L0 = make_layout(p.lcap, fp64 ? 8 : 4, (int)elem, gs, 0);
+    const Layout L0 = make_layout(p.lcap, fp64 ? 8 : 4, (int)elem, perf, 0);
     int64_t stage = ((int64_t)g->max_smem - L0.total - SWEEP_STATIC_SMEM) / (int64_t)elem;
     stage = it.stage_kb > 0 ? std::min<int64_t>(stage, (int64_t)it.stage_kb * 1024 / elem) : 0;
     p.stage = (int32_t)std::max<int64_t>(0, std::min<int64_t>(g->n, stage));
@@ -132,7 +136,7 @@ template <typename T, typename A>
 pr_status make_plan(pr_graph *g, const SweepParams &p, bool gs, SweepPlan &plan)
 {
     plan.func = pick_sweep<T, A>(gs, p.ew != nullptr);
-    plan.smem = gs ? layout_of<T, A, true>(p).total : layout_of<T, A, false>(p).total;
+    plan.smem = layout_of<T, A, false>(p).total;
     // fused sweep: the hottest items (hub segments and the widest mid
     // groups) first, so the rest reads their new values; one launch only
     // where pr_tune.fused_split asks for it
@@ -332,8 +336,13 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
         set_error("the deterministic fused sweep needs FP64, an unweighted graph and n <= 65536");
         return PR_ERR_UNSUPPORTED;
     }
+    const bool perf = o->perforate_eps > 0.0;
+    if (perf && (gs || weighted)) {
+        set_error("loop perforation needs the Jacobi sweep and an unweighted graph");
+        return PR_ERR_UNSUPPORTED;
+    }
     SweepParams p;
-    fill_params(g, p, fp64, sizeof(T), gs);
+    fill_params(g, p, fp64, sizeof(T), perf);
     const int32_t *n2o = g->n2o.as<int32_t>();
     const int32_t *o2n = g->o2n.as<int32_t>();
     if (serial) {  // strict Eq. 9 order on the input ids
@@ -351,11 +360,23 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
         plan.p[0] = p;
         plan.grid[0] = 1;
         plan.block = 32;
+    } else if (perf) {
+        PR_TRY(buf_alloc(g, g->lastbuf, (size_t)g->n * sizeof(A) + 256, s));
+        p.last = g->lastbuf.p;
+        plan.func = reinterpret_cast<const void *>(&k_sweep_perf<T, A>);
+        plan.smem = layout_of<T, A, true>(p).total;
+        plan.nlaunch = 1;
+        plan.p[0] = p;
+        plan.grid[0] = sweep_grid(g, p.item_hi, plan.func, plan.smem);
+        if (plan.grid[0] == 0) return PR_ERR_INVALID_ARG;
     } else {
         PR_TRY((make_plan<T, A>(g, p, gs, plan)));
     }
     SolveState *hs = g->host_state;
     init_state(g, o, *hs);
+    hs->perf = perf ? 1 : 0;
+    hs->perf_period = o->perforate_period;
+    hs->perf_eps = o->perforate_eps;
     PR_CUDA(cudaMemcpyAsync(g->state.p, hs, sizeof(SolveState), cudaMemcpyHostToDevice, s));
     const int ib = std::max(1, std::min<int>((g->n + 255) / 256, g->num_sms * 8));
     k_init<T, A><<<ib, 256, 0, s>>>(g->n, o->x0, n2o, p.outdeg, static_cast<const A *>(p.inv),
@@ -366,7 +387,8 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
     bool graph_loop = false;
     if (o->use_graph) {
         const int key = (fp64 ? 1 : 0) | (gs ? 2 : 0) | (serial ? 4 : 0) | (weighted ? 8 : 0) |
-                        (g->items.test_stall ? 32 : 0) | (p.renorm ? 128 : 0);
+                        (g->items.test_stall ? 32 : 0) | (p.renorm ? 128 : 0) |
+                        (perf ? 256 : 0);
         cudaGraphExec_t exec;
         PR_TRY(loop_graph(g, key, plan, &exec));
         PR_CUDA(cudaGraphLaunch(exec, s));
@@ -389,6 +411,7 @@ static pr_status solve_plain(pr_graph *g, const pr_options *o, const pr_tune &tn
     note_launch();
     PR_LAUNCH_CHECK();
     pr_status st = finish_result(g, res, s, 0);
+    if (res) res->gathered = perf ? (int64_t)g->host_state->gathered : (int64_t)res->iters * g->m;
     // loop sweeps + the launch that sees the stop flag
     if (graph_loop) note_launch((uint64_t)plan_launches(plan) * (g->host_state->iter + 1));
     return st;
@@ -441,6 +464,10 @@ extern "C" pr_status pr_solve(pr_graph *g, const pr_options *o, double *x_out, p
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     pr_tune tn;
     PR_TRY(prepare_solve(g, o, tn, s));
+    if (o->perforate_eps > 0.0 && o->precision != PR_FP64 && o->precision != PR_FP32) {
+        set_error("loop perforation needs PR_FP64 or PR_FP32");
+        return PR_ERR_UNSUPPORTED;
+    }
     switch (o->precision) {
     case PR_FP64: return solve_plain<double, double>(g, o, tn, x_out, res, s);
     case PR_FP32: return solve_plain<float, float>(g, o, tn, x_out, res, s);

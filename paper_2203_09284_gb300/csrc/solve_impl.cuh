@@ -15,7 +15,7 @@ pr_status prepare_solve(pr_graph *g, const pr_options *o, pr_tune &tn, cudaStrea
 // Sweep parameters over the degree-ordered in-lists; stored vectors of
 // `elem` bytes per vertex in ybuf; the staged copy takes the shared memory
 // left beside the warp slices of this arithmetic (fp64) and variant (gs).
-void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool gs);
+void fill_params(pr_graph *g, SweepParams &p, bool fp64, size_t elem, bool perf);
 
 // Grid of a persistent sweep kernel over `nitems` warp items with `smem`
 // bytes of dynamic shared memory (0 with the error set if it does not fit).

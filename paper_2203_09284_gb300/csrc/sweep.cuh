@@ -44,13 +44,19 @@
 // Jacobi (Algorithm 1, Eq. 2): reads y[iter & 1], writes the other buffer.
 // Fused (Algorithm 2, Eq. 9): one buffer updated in place, so a vertex sees
 // whichever contribution is there (new if its in-neighbour was already
-// updated in this sweep).  The hottest vertices (hubs and the mid vertices
-// with more than 128 in-edges) are updated by a first launch, so the second
-// launch's shared-memory copy and loads already see their new values; inside
-// a low tile, a vertex reads the new values of the tile's earlier vertices.
-// After each fused sweep the iterate is rescaled to sum 1 by folding 1/sum
-// into sigma.
+// updated in this sweep and the store has reached the load's cache level).
+// The hottest vertices (hubs and the mid vertices with more than 128
+// in-edges) are updated by a first launch, so the second launch's
+// shared-memory copy and loads already see their new values; a low tile's
+// in-edges are all gathered before any of its vertices is updated.  After
+// each fused sweep the iterate is rescaled to sum 1 by folding 1/sum into
+// sigma (unless the solve asks for the literal Algorithm 2).
+// Perforated Jacobi (loop perforation): the epilogue functor decides per
+// vertex whether it keeps its value; a kept vertex's in-edges are not
+// gathered (low tiles mark their slots in a per-warp bit mask).
 #pragma once
+
+#include <type_traits>
 
 #include "common.cuh"
 #include "tma.cuh"
@@ -100,6 +106,7 @@ struct SweepParams {
     int32_t renorm;               // fused sweep: rescale to sum 1
     int32_t dc;                   // correction sweep of a defect-correction solve
     int32_t shift;                // correction sweep: restore the exact sum of e
+    void *last;                   // perforated sweep: A[n] last change per vertex
 };
 
 // Loads of the stored vector.  Jacobi: read-only path (the kernel never
@@ -251,6 +258,59 @@ struct SweepFin {
     }
 };
 
+// Perforated Jacobi sweep: a vertex whose change at its last computation was
+// below eps times its value keeps the value in a perforated sweep (keep():
+// no gather; its stored value is carried to the output buffer); computed
+// vertices record their change.  The first sweep and every period-th are
+// full (st->perf_period).
+template <typename F, typename = void>
+struct perf_of : std::false_type {};
+template <typename F>
+struct perf_of<F, std::void_t<decltype(F::PERF)>> : std::bool_constant<F::PERF> {};
+
+template <typename T, typename A>
+struct SweepFinPerf : SweepFin<T, A, false, false> {
+    static constexpr bool PERF = true;
+    A *last;        // [n] change at the last computation (true units)
+    A eps;
+    bool full;
+    unsigned long long gath = 0;  // in-list entries this thread summed
+    __device__ SweepFinPerf(const SweepParams &p_, const Ctx<A> &c_, T *yo, A *last_, A eps_,
+                            bool full_)
+        : SweepFin<T, A, false, false>(p_, c_, yo), last(last_), eps(eps_), full(full_) {}
+    __device__ __forceinline__ bool skip(int u, int od, T yold) const
+    {
+        if (full) return false;
+        const A yo = to_a<A>(yold);
+        const A x = this->c.sig * (od == 0 ? yo : yo * static_cast<A>(od));
+        return last[u] < eps * x;
+    }
+    __device__ __forceinline__ T operator()(int u, A acc, int od, A inv, T yold, A r)
+    {
+        const A yo = to_a<A>(yold);
+        const A xold = od == 0 ? yo : yo * static_cast<A>(od);
+        const A xnew = r + this->c.d * (this->c.sig * (acc + this->c.dt));
+        const A diff = aabs(xnew - this->c.sig * xold);
+        const A xs = xnew * this->c.rsig;
+        const T yn = from_a<T>(od == 0 ? xs : xs * inv);
+        this->yout[u] = yn;
+        last[u] = diff;
+        this->pt.l1 += diff;
+        this->pt.lmax = diff > this->pt.lmax ? diff : this->pt.lmax;
+        this->pt.sm += xs;
+        if (od == 0) this->pt.dm += xs;
+        return yn;
+    }
+    __device__ __forceinline__ void keep(int u, int od, T yold)
+    {
+        const A yo = to_a<A>(yold);
+        const A xs = od == 0 ? yo : yo * static_cast<A>(od);
+        this->yout[u] = yold;
+        this->pt.sm += xs;
+        if (od == 0) this->pt.dm += xs;
+    }
+};
+
 // Reduces the block's partial sums and adds them to the sweep accumulators.
 template <typename A>
 __device__ __forceinline__ void block_partials(SolveState *st, const Part<A> &pt)
@@ -356,6 +416,8 @@ __device__ __forceinline__ void close_sweep(const SweepParams &p)
     if (!p.dc) {
         if (st->history) st->history[it - 1] = err;
         conv = err <= st->tau;
+        // a perforated solve with a period stops only after a full sweep
+        if (st->perf && st->perf_period > 0) conv = conv && ((it - 1) % st->perf_period == 0);
         stop = conv || it >= st->max_iter || error;
         st->status = error ? error : (conv ? PR_OK : PR_NOT_CONVERGED);
     } else {
@@ -401,27 +463,27 @@ __host__ __device__ constexpr uint32_t a16(size_t b) { return (uint32_t)((b + 15
 
 // Dynamic shared memory of a sweep block:
 //   [staged y[0, stage)] [barriers] [32 warp slices]
-// and of one warp slice: [gathered terms, lcap].
+// and of one warp slice: [gathered terms, lcap] [perforated sweeps: one bit
+// per term, set for the in-edges of vertices that keep their value].
 struct Layout {
-    uint32_t bars, warps, wvals, wbytes, total;
+    uint32_t bars, warps, wmask, wbytes, total;
 };
 
-__host__ __device__ inline Layout make_layout(int lcap, int sa, int st, bool gs, int stage)
+__host__ __device__ inline Layout make_layout(int lcap, int sa, int st, bool perf, int stage)
 {
     Layout L;
     L.bars = a16((size_t)stage * st);
     L.warps = L.bars + 32;
-    L.wvals = 0;
-    L.wbytes = a16((size_t)lcap * sa);
+    L.wmask = a16((size_t)lcap * sa);
+    L.wbytes = L.wmask + (perf ? a16((size_t)((lcap + 31) / 32) * 4) : 0);
     L.total = L.warps + SWEEP_WARPS * L.wbytes;
-    (void)gs;
     return L;
 }
 
-template <typename T, typename A, bool GS>
+template <typename T, typename A, bool PERF>
 __host__ __device__ inline Layout layout_of(const SweepParams &p)
 {
-    return make_layout(p.lcap, sizeof(A), sizeof(T), GS, p.stage);
+    return make_layout(p.lcap, sizeof(A), sizeof(T), PERF, p.stage);
 }
 
 // Where a gathered contribution comes from: the copy of y[0, nstaged) in
@@ -497,9 +559,14 @@ __device__ __forceinline__ void hub_item(const SweepParams &p, int i, const int4
                                          const Src<T, GS> &src, Fin &fin, int lane)
 {
     const int h = d.x;
-    A acc = group_stream<32, T, A, GS, W>(p, src, d.z, d.w, lane);
+    bool sk = false;
+    if constexpr (perf_of<Fin>::value) sk = fin.skip(h, __ldg(p.outdeg + h), ld_y<T, GS>(src.y, h));
+    A acc = sk ? A(0) : group_stream<32, T, A, GS, W>(p, src, d.z, d.w, lane);
     const double s = warp_sum(static_cast<double>(acc));
     if (lane == 0) {
+        if constexpr (perf_of<Fin>::value) {
+            if (!sk) fin.gath += (unsigned long long)(d.w - d.z);
+        }
         p.seg_acc[i] = s;
         __threadfence();
         const int s0 = p.hubseg_start[h];
@@ -510,6 +577,12 @@ __device__ __forceinline__ void hub_item(const SweepParams &p, int i, const int4
             double all = 0;
             for (int j = 0; j < nseg; ++j) all += sa[s0 + j];
             p.hub_cnt[h] = 0;
+            if constexpr (perf_of<Fin>::value) {
+                if (sk) {
+                    fin.keep(h, p.outdeg[h], ld_y<T, GS>(src.y, h));
+                    return;
+                }
+            }
             fin(h, static_cast<A>(all), p.outdeg[h], static_cast<const A *>(p.inv)[h],
                 ld_y<T, GS>(src.y, h), rhs_of<A>(p, h, fin.base()));
         }
@@ -537,9 +610,24 @@ __device__ __forceinline__ void mid_group(const SweepParams &p, int v0, int v_en
             r = rhs_of<A>(p, u, fin.base());
         }
     }
+    bool sk = false;
+    if constexpr (perf_of<Fin>::value) {
+        // the group's first lane decides; a kept vertex gathers nothing
+        sk = __shfl_sync(FULL, (act && gl == 0) ? fin.skip(u, od, yo) : false, lane & ~(G - 1));
+        if (sk) e = a;
+        if (act && gl == 0 && !sk) fin.gath += (unsigned long long)(e - a);
+    }
     A acc = group_stream<G, T, A, GS, W>(p, src, a, e, gl);
     acc = group_sum<G>(acc);
-    if (act && gl == 0) fin(u, acc, od, inv, yo, r);
+    if (act && gl == 0) {
+        if constexpr (perf_of<Fin>::value) {
+            if (sk) {
+                fin.keep(u, od, yo);
+                return;
+            }
+        }
+        fin(u, acc, od, inv, yo, r);
+    }
 }
 
 // low tile k (one warp): in-edges gathered into the warp's shared slice,
@@ -550,7 +638,9 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
                                          unsigned char *slice, const Layout &L)
 {
     const int v0 = d.x, v1 = d.y, ea = d.z, eb = d.w;
-    A *vals = reinterpret_cast<A *>(slice + L.wvals);
+    constexpr bool PF = perf_of<Fin>::value;
+    A *vals = reinterpret_cast<A *>(slice);
+    uint32_t *mask = reinterpret_cast<uint32_t *>(slice + L.wmask);
     const A *ew = static_cast<const A *>(p.ew);
     // inputs of this lane's first vertex, issued before the gathers
     int u = v0 + lane;
@@ -565,6 +655,36 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
         yo0 = ld_y<T, GS>(src.y, u);
         r0 = rhs_of<A>(p, u, fin.base());
     }
+    if constexpr (PF) {
+        // slots of the vertices that keep their value: one bit each (a low
+        // vertex has at most 32 in-edges, so its run spans at most 2 words)
+        for (int w = lane; w < ((eb - ea + 31) >> 5); w += 32) mask[w] = 0;
+        __syncwarp();
+        for (int u0 = v0; u0 < v1; u0 += 32) {
+            const int uu = u0 + lane;
+            if (uu < v1) {
+                int a = a0, e = e0;
+                bool sk;
+                if (u0 == v0) {
+                    sk = fin.skip(uu, od0, yo0);
+                } else {
+                    a = __ldg(p.col_ptr + uu);
+                    e = __ldg(p.col_ptr + uu + 1);
+                    sk = fin.skip(uu, __ldg(p.outdeg + uu), ld_y<T, GS>(src.y, uu));
+                }
+                if (sk && e > a) {
+                    const int lo = a - ea, hi = e - ea, len = hi - lo;
+                    const uint32_t run = len >= 32 ? ~0u : ((1u << len) - 1u);
+                    atomicOr(&mask[lo >> 5], run << (lo & 31));
+                    if (((hi - 1) >> 5) != (lo >> 5)) {
+                        const int rem = hi - ((hi - 1) >> 5) * 32;
+                        atomicOr(&mask[(hi - 1) >> 5], rem >= 32 ? ~0u : ((1u << rem) - 1u));
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
     // gathers: eight slots per lane in flight
     const uint64_t pol = policy_stream();
     for (int j0 = (ea & ~3) + 4 * lane; j0 < eb; j0 += 256) {
@@ -576,7 +696,9 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int s = (c < 4 ? j0 : j1) + (c & 3);
-            got[c] = (s >= ea && s < eb) ? to_a<A>(src(v[c])) : A(0);
+            bool take = s >= ea && s < eb;
+            if constexpr (PF) take = take && !((mask[(s - ea) >> 5] >> ((s - ea) & 31)) & 1u);
+            got[c] = take ? to_a<A>(src(v[c])) : A(0);
         }
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -602,6 +724,13 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
                 inv = __ldg(static_cast<const A *>(p.inv) + u);
                 yo = ld_y<T, GS>(src.y, u);
                 r = rhs_of<A>(p, u, fin.base());
+            }
+            if constexpr (PF) {
+                if (fin.skip(u, od, yo)) {
+                    fin.keep(u, od, yo);
+                    continue;
+                }
+                fin.gath += (unsigned long long)(e - a);
             }
             A acc = 0;
             for (int i = a - ea; i < e - ea; ++i) acc += vals[i];
@@ -630,7 +759,7 @@ template <typename T, typename A, bool GS, bool W, typename Fin>
 __device__ __forceinline__ void run_items(const SweepParams &p, const T *yin, Fin &fin)
 {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    const Layout L = layout_of<T, A, GS>(p);
+    const Layout L = layout_of<T, A, perf_of<Fin>::value>(p);
     uint64_t *bars = reinterpret_cast<uint64_t *>(dyn_smem + L.bars);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t limit = p.wait_limit ? p.wait_limit : DEFAULT_WAIT_LIMIT;
@@ -707,6 +836,32 @@ __global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_sweep(SweepParams p)
     }
     SweepFin<T, A, GS, W> fin(p, load_ctx<A>(st), yout);
     run_items<T, A, GS, W>(p, yin, fin);
+    block_partials<A>(st, fin.pt);
+    if (p.close && last_block(st) && threadIdx.x < 32) close_sweep(p);
+}
+
+// Perforated Jacobi sweep (one launch per sweep).  The counts of gathered
+// in-list entries are added to st->gathered.
+template <typename T, typename A>
+__global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_sweep_perf(SweepParams p)
+{
+    SolveState *st = p.st;
+    if (st->done) {
+        if (p.close && p.use_cond && blockIdx.x == 0 && threadIdx.x == 0)
+            cudaGraphSetConditional(p.cond, 0u);
+        return;
+    }
+    const int iter = st->iter;
+    const T *yin = static_cast<const T *>((iter & 1) ? p.y1 : p.y0);
+    T *yout = static_cast<T *>((iter & 1) ? p.y0 : p.y1);
+    const bool full = iter == 0 || (st->perf_period > 0 && iter % st->perf_period == 0);
+    SweepFinPerf<T, A> fin(p, load_ctx<A>(st), yout, static_cast<A *>(p.last),
+                           static_cast<A>(st->perf_eps), full);
+    run_items<T, A, false, false>(p, yin, fin);
+    unsigned long long g = fin.gath;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(FULL, g, o);
+    if ((threadIdx.x & 31) == 0 && g) atomicAdd(&st->gathered, g);
     block_partials<A>(st, fin.pt);
     if (p.close && last_block(st) && threadIdx.x < 32) close_sweep(p);
 }
