@@ -130,8 +130,8 @@ typedef struct {
                                on the device; 0: host-driven loop */
     int32_t max_outer;      /* *_DC: max FP64 residual evaluations (default 8) */
     double inner_rel;       /* *_DC: inner stop, relative to ||r||_1 (0: auto:
-                               FP32 1e-5 Jacobi / 3e-5 fused, FP16 4e-3,
-                               BF16 3e-2); an inner solve also stops once its
+                               FP32 1e-5 Jacobi / 3e-5 fused, FP16 and BF16
+                               1e-2); an inner solve also stops once its
                                change has not fallen for 8 sweeps */
     const pr_tune *tune;    /* NULL: the graph's defaults */
     int32_t no_rescale;     /* PR_FUSED_GS with PR_FP64 / PR_FP32: 1 runs the
@@ -193,11 +193,18 @@ pr_status pr_options_default(pr_options *o);
  *           (unweighted).
  *           Weighted graphs use P_uv = w_uv / sum_v' w_uv'.
  *   flags   PR_BUILD_CSR also builds the out-lists (needed by pr_backward;
- *           built lazily otherwise).
+ *           built lazily otherwise).  PR_DEDUP keeps only the first
+ *           occurrence (lowest input position) of each repeated (u, v) pair
+ *           (the paper's workloads are simple graphs, Sec. 5.2); the graph's
+ *           edge count (pr_graph_info, the exported lists) is then the number
+ *           kept, csc_eid/csr_eid still give input positions, weights of
+ *           dropped edges are ignored and their pr_backward gradient is 0.
+ *           Without it repeated edges count with multiplicity.
  *   alloc   allocator hooks or NULL (cudaMallocAsync); kept by the graph.
  *   out     receives the handle (NULL on error).
  */
 #define PR_BUILD_CSR 1u
+#define PR_DEDUP 2u
 pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                           const float *w, uint32_t flags, const pr_allocator *alloc,
                           void *stream, pr_graph **out);
@@ -238,22 +245,31 @@ pr_status pr_solve(pr_graph *g, const pr_options *o, double *x_out, pr_result *r
 
 /*
  * Personalised PageRank for B teleport vectors at once (multi right-hand
- * side sweep): column b teleports to the single vertex seeds[b] and its
- * dangling mass is redistributed to the same vertex.  Jacobi sweep in FP32
- * or FP64 (o->precision PR_FP32 or PR_FP64, o->variant PR_JACOBI, L1 norm);
- * each column stops on its own L1 change and keeps that iterate.  An FP32
- * column whose change stops decreasing above the threshold (its rounding
- * floor) stops too, with status PR_NOT_CONVERGED.  Start vector 1/n.
- *   seeds  device int32 [B], ids in [0, n)
- *   X_out  device [n][B] (vertex-major, column b at stride B) of float for
- *          PR_FP32 or double for PR_FP64, each column normalised to sum 1
+ * side sweep): Eq. 1 with the uniform teleport (1-d)/n replaced by
+ * (1-d) v_b for each column b.  Either seeds (column b teleports to the
+ * single vertex seeds[b]) or V (dense teleport vectors) is given, not both;
+ * a column's dangling mass is redistributed along its own teleport vector,
+ * so every column sums to 1.  Jacobi sweep in FP32 or FP64 (o->precision
+ * PR_FP32 or PR_FP64, o->variant PR_JACOBI, L1 norm); each column stops on
+ * its own L1 change and keeps that iterate.  An FP32 column whose change
+ * stops decreasing above the threshold (its rounding floor) stops too, with
+ * status PR_NOT_CONVERGED.  Start vector 1/n.
+ *   seeds  device int32 [B], ids in [0, n), or NULL
+ *   V      device [n][B] (vertex-major, column b at stride B) of float for
+ *          PR_FP32 or double for PR_FP64, or NULL: teleport vectors, entries
+ *          finite and >= 0 (PR_ERR_INVALID_ARG otherwise), each column
+ *          summing to 1 (not checked; a column with another sum S solves the
+ *          problem with teleport mass S(1-d))
+ *   X_out  device [n][B] (same layout and type as V): each column
+ *          normalised to sum 1
  *   res    host [B], nullable: per-column sweeps, last change, status
  * Returns PR_OK if every column converged, else PR_NOT_CONVERGED (outputs
- * still written) or an error.  Columns run in passes of 256 (FP32) or 128
- * (FP64); the handle keeps two n x pass-width iterates.
+ * still written) or an error.  Columns run in passes of at most 256 (FP32)
+ * or 128 (FP64); the handle keeps two n x pass-width iterates (and the
+ * pass's teleport rows when V is given).
  */
 pr_status pr_solve_batched(pr_graph *g, const pr_options *o, int32_t B, const int32_t *seeds,
-                           void *X_out, pr_result *res, void *stream);
+                           const void *V, void *X_out, pr_result *res, void *stream);
 
 /*
  * Solves G independent graphs in one sequence of launches (each sweep is one
@@ -275,7 +291,8 @@ pr_status pr_solve_multi(pr_graph *const *graphs, int32_t G, const pr_options *o
  *     dL/dd   = lambda^T (M x - 1/n)
  * (raw weights w with row sums s_u; unweighted graphs use w = 1).
  *   x, grad_x  device double [n]
- *   grad_w     device double [m] in input edge order, or NULL
+ *   grad_w     device double [m] in input edge order (m = pr_graph_create's
+ *              edge count), or NULL
  *   grad_d     device double [1], or NULL
  * o->threshold applies to the L1 change of lambda per sweep.
  */

@@ -21,6 +21,7 @@ __all__ = [
     "PR_OK", "PR_ERR_INVALID_ARG", "PR_ERR_OOM", "PR_ERR_CUDA", "PR_NOT_CONVERGED",
     "PR_ERR_TIMEOUT", "PR_ERR_UNSUPPORTED", "PR_ERR_NUMERIC", "PR_JACOBI", "PR_FUSED_GS", "PR_FP64", "PR_FP32",
     "PR_FP32_DC", "PR_BF16_DC", "PR_FP16_DC", "PR_NORM_L1", "PR_NORM_LINF", "PR_BUILD_CSR",
+    "PR_DEDUP",
     "PrOptions", "PrResult", "PrTune", "PrAllocator", "PageRankError", "lib", "library_path",
     "pr_options_default", "pr_graph_create", "pr_graph_destroy", "pr_graph_info",
     "pr_graph_export", "pr_solve", "pr_solve_batched", "pr_solve_multi", "pr_backward",
@@ -33,6 +34,7 @@ PR_JACOBI, PR_FUSED_GS = 0, 1
 PR_FP64, PR_FP32, PR_FP32_DC, PR_BF16_DC, PR_FP16_DC = 0, 1, 2, 3, 4
 PR_NORM_L1, PR_NORM_LINF = 0, 1
 PR_BUILD_CSR = 1
+PR_DEDUP = 2
 
 VARIANTS = {"jacobi": PR_JACOBI, "gs": PR_FUSED_GS, "fused_gs": PR_FUSED_GS}
 PRECISIONS = {"fp64": PR_FP64, "fp32": PR_FP32, "fp32_dc": PR_FP32_DC, "bf16_dc": PR_BF16_DC,
@@ -114,7 +116,7 @@ def lib():
                                         ctypes.POINTER(i32), ctypes.POINTER(i32)]
             L.pr_graph_export.argtypes = [vp] + [vp] * 12 + [vp]
             L.pr_solve.argtypes = [vp, ctypes.POINTER(PrOptions), vp, ctypes.POINTER(PrResult), vp]
-            L.pr_solve_batched.argtypes = [vp, ctypes.POINTER(PrOptions), i32, vp, vp,
+            L.pr_solve_batched.argtypes = [vp, ctypes.POINTER(PrOptions), i32, vp, vp, vp,
                                            ctypes.POINTER(PrResult), vp]
             L.pr_solve_multi.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(PrOptions),
                                          ctypes.POINTER(vp), ctypes.POINTER(PrResult), vp]
@@ -294,11 +296,13 @@ def pr_solve(handle, options, x_out, stream=None):
     return r
 
 
-def pr_solve_batched(handle, options, seeds, X_out, stream=None):
-    B = int(seeds.numel())
+def pr_solve_batched(handle, options, seeds, X_out, stream=None, V=None):
+    """Personalised PageRank of B columns: one-hot seeds (int32 [B]) or dense
+    teleport vectors V ([n][B], X_out's type); returns B PrResults."""
+    B = int(seeds.numel()) if seeds is not None else int(V.shape[1])
     res = (PrResult * max(B, 1))()
     st = lib().pr_solve_batched(ctypes.c_void_p(handle), ctypes.byref(options), B, _ptr(seeds),
-                                _ptr(X_out), res, _stream(stream))
+                                _ptr(V), _ptr(X_out), res, _stream(stream))
     _check(st, "pr_solve_batched", ok=(PR_OK, PR_NOT_CONVERGED))
     return list(res)[:B]
 
@@ -341,12 +345,12 @@ class Graph:
     pinned host memory."""
 
     def __init__(self, n, src, dst, w=None, build_csr=False, use_torch_allocator=True,
-                 stream=None):
+                 stream=None, dedup=False):
         self.n = int(n)
-        self.m = int(src.numel())
+        self.m = int(src.numel())  # input edges (pr_backward's grad_w length)
         alloc = _TORCH_ALLOCATOR if use_torch_allocator else None
-        self.handle = pr_graph_create(n, src, dst, w, PR_BUILD_CSR if build_csr else 0, alloc,
-                                      stream)
+        flags = (PR_BUILD_CSR if build_csr else 0) | (PR_DEDUP if dedup else 0)
+        self.handle = pr_graph_create(n, src, dst, w, flags, alloc, stream)
         self.weighted = w is not None
 
     def close(self):
@@ -371,12 +375,12 @@ class Graph:
         res = pr_solve(self.handle, make_options(**kw), x, stream)
         return x, res
 
-    def solve_batched(self, seeds, out=None, stream=None, **kw):
+    def solve_batched(self, seeds=None, out=None, stream=None, V=None, **kw):
         kw.setdefault("precision", "fp32")
-        B = int(seeds.numel())
+        B = int(seeds.numel()) if seeds is not None else int(V.shape[1])
         dt = torch.float64 if kw["precision"] == "fp64" else torch.float32
         X = out if out is not None else torch.empty((self.n, B), dtype=dt, device="cuda")
-        res = pr_solve_batched(self.handle, make_options(**kw), seeds, X, stream)
+        res = pr_solve_batched(self.handle, make_options(**kw), seeds, X, stream, V=V)
         return X, res
 
     def backward(self, x, grad_x, stream=None, want_w=True, want_d=True, **kw):

@@ -273,6 +273,9 @@ static pr_status backward(pr_graph *g, const pr_options *o, const double *x,
     q.d = o->d;
     q.grad_w = grad_w;
     q.grad_d = grad_d;
+    // repeated edges dropped by PR_DEDUP take no part: their gradient is 0
+    if (grad_w && g->m_in != g->m)
+        PR_CUDA(cudaMemsetAsync(grad_w, 0, sizeof(double) * (size_t)g->m_in, s));
     q.st = rev->state.as<SolveState>();
     const T *lam = static_cast<const T *>((hs->iter & 1) ? p.y1 : p.y0);
     k_adj_grad<T><<<g->num_sms * 4, 256, 0, s>>>(q, lam);

@@ -5,7 +5,9 @@
 // sends its dangling mass there too (Eq. 1 with the uniform teleport 1/n
 // replaced by the unit vector of s_b):
 //   x'_b(u) = d * sum_{v in in(u)} P_vu x_b(v) + [u == s_b] ((1-d) + d D_b),
-//   D_b     = sum_{v dangling} x_b(v).
+//   D_b     = sum_{v dangling} x_b(v),
+// or, with dense teleport vectors V (column b sums to 1), along V:
+//   x'_b(u) = d * sum_{v in in(u)} P_vu x_b(v) + V_b(u) ((1-d) + d D_b).
 // The sweep is Jacobi (Algorithm 1 applied to every column) in FP32 or FP64
 // (rows and sums in that type).  A column stops after the sweep whose L1
 // change is <= threshold and keeps that iterate (later sweeps copy it
@@ -72,6 +74,8 @@ struct BatchParams {
     double *best;             // [Bp] smallest L1 change so far
     int32_t *since;           // [Bp] sweeps since the smallest change
     int32_t stall;            // stop columns at their rounding floor (FP32)
+    const void *tele_rows;    // E[n][Bp] dense teleport rows (degree-ordered ids)
+                              // or null: one-hot seeds
     BatchState *st;
     cudaGraphConditionalHandle cond;
     int32_t use_cond;
@@ -211,14 +215,17 @@ __device__ __forceinline__ void batch_fin(const BatchParams &p, int u, const E (
 {
     using IO = RowIO<E, VEC>;
     constexpr int BP = IO::BP;
-    E xo[VEC], xn[VEC];
+    E xo[VEC], xn[VEC], tv[VEC];
     IO::template load<false>(xin + (size_t)u * BP, lane, xo);
+    const E *trow = static_cast<const E *>(p.tele_rows);
+    if (trow) IO::template load<false>(trow + (size_t)u * BP, lane, tv);
     const bool dangling = __ldg(p.outdeg + u) == 0;
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
         const int b = IO::col(lane, k);
         E v = d * acc[k];
-        if (sh.seed[b] == u) v += sh.tele[b];
+        if (trow) v += tv[k] * sh.tele[b];
+        else if (sh.seed[b] == u) v += sh.tele[b];
         if (sh.frozen[b]) v = xo[k];
         xn[k] = v;
         sh.werr[b] += fabs((double)v - (double)xo[k]);
@@ -406,7 +413,7 @@ __global__ void k_batch_init(BatchParams p, const int32_t *__restrict__ seeds,
     if (blockIdx.x == 0)
         for (int t = threadIdx.x; t < BP; t += blockDim.x) {
             int sd = -1;
-            if (t < ncols) {
+            if (t < ncols && seeds) {
                 const int s = seeds[t];
                 if (s < 0 || s >= p.n) atomicOr(bad, 1);
                 else sd = o2n[s];
@@ -419,6 +426,26 @@ __global__ void k_batch_init(BatchParams p, const int32_t *__restrict__ seeds,
             p.since[t] = 0;
             p.acc[4 * t] = p.acc[4 * t + 1] = p.acc[4 * t + 2] = p.acc[4 * t + 3] = 0;
         }
+}
+
+// Dense teleport rows of the pass in the degree-ordered ids:
+// out[k][b] = V[n2o[k]][c0 + b] for the pass's columns, 0 in the padding;
+// flag 2 in *bad for a negative or non-finite entry.
+template <typename E, int BP>
+__global__ void k_batch_tele(int32_t n, const E *__restrict__ V, int ld, int c0, int ncols,
+                             const int32_t *__restrict__ n2o, E *out, int32_t *bad)
+{
+    const size_t total = (size_t)n * BP;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(i / BP), b = (int)(i % BP);
+        E v = E(0);
+        if (b < ncols) {
+            v = V[(size_t)n2o[k] * ld + c0 + b];
+            if (!(v >= E(0)) || isinf((double)v)) atomicOr(bad, 2);
+        }
+        out[i] = v;
+    }
 }
 
 // Column sums of the final iterate (exact fixed-point accumulation).
@@ -510,8 +537,8 @@ static pr_status ensure_batch_items(pr_graph *g, cudaStream_t s)
 static size_t cols_bytes() { return (size_t)BATCH_COLS * (32 + 3 * 8 + 3 * 4) + 256; }
 
 template <typename E, int VEC>
-static pr_status batch_pass(pr_graph *g, const pr_options *o, const int32_t *seeds, int ncols,
-                            int ld, int c0, E *X_out, pr_result *res, cudaStream_t s)
+static pr_status batch_pass(pr_graph *g, const pr_options *o, const int32_t *seeds, const E *V,
+                            int ncols, int ld, int c0, E *X_out, pr_result *res, cudaStream_t s)
 {
     constexpr int BP = 32 * VEC;
     constexpr bool fp64 = sizeof(E) == 8;
@@ -555,14 +582,23 @@ static pr_status batch_pass(pr_graph *g, const pr_options *o, const int32_t *see
     PR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
     const double dang0 = (double)g->n_dangling * (double)(E)(1.0 / (double)n);
     const int ib = std::max(1, std::min<int>((int)(((size_t)n * BP + 255) / 256), g->num_sms * 8));
-    k_batch_init<E, BP><<<ib, 256, 0, s>>>(p, seeds + c0, g->o2n.as<int32_t>(), ncols, dang0, bad);
+    k_batch_init<E, BP><<<ib, 256, 0, s>>>(p, seeds ? seeds + c0 : nullptr, g->o2n.as<int32_t>(),
+                                           ncols, dang0, bad);
     note_launch();
+    if (V) {
+        PR_TRY(buf_alloc(g, g->btele, (size_t)n * BP * sizeof(E), s));
+        k_batch_tele<E, BP><<<ib, 256, 0, s>>>(n, V, ld, c0, ncols, g->n2o.as<int32_t>(),
+                                               g->btele.as<E>(), bad);
+        note_launch();
+        p.tele_rows = g->btele.p;
+    }
     PR_LAUNCH_CHECK();
     int32_t hbad = 0;
     PR_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
     if (hbad) {
-        set_error("pr_solve_batched: a seed lies outside [0, %d)", n);
+        if (hbad & 1) set_error("pr_solve_batched: a seed lies outside [0, %d)", n);
+        else set_error("pr_solve_batched: teleport entries must be finite and non-negative");
         return PR_ERR_INVALID_ARG;
     }
 
@@ -661,7 +697,7 @@ static pr_status batch_pass(pr_graph *g, const pr_options *o, const int32_t *see
 
 template <typename E>
 static pr_status solve_batched(pr_graph *g, const pr_options *o, int32_t B, const int32_t *seeds,
-                               E *X_out, pr_result *res, cudaStream_t s)
+                               const E *V, E *X_out, pr_result *res, cudaStream_t s)
 {
     constexpr int MAXC = sizeof(E) == 8 ? 128 : 256;  // columns per pass
     const int first = std::min<int>(B, MAXC);
@@ -675,10 +711,10 @@ static pr_status solve_batched(pr_graph *g, const pr_options *o, int32_t B, cons
     for (int c0 = 0; c0 < B; c0 += MAXC) {
         const int nc = std::min<int>(MAXC, B - c0);
         pr_status st;
-        if (nc <= 32) st = batch_pass<E, 1>(g, o, seeds, nc, B, c0, X_out, res, s);
-        else if (nc <= 64) st = batch_pass<E, 2>(g, o, seeds, nc, B, c0, X_out, res, s);
-        else if (nc <= 128) st = batch_pass<E, 4>(g, o, seeds, nc, B, c0, X_out, res, s);
-        else if constexpr (MAXC > 128) st = batch_pass<E, 8>(g, o, seeds, nc, B, c0, X_out, res, s);
+        if (nc <= 32) st = batch_pass<E, 1>(g, o, seeds, V, nc, B, c0, X_out, res, s);
+        else if (nc <= 64) st = batch_pass<E, 2>(g, o, seeds, V, nc, B, c0, X_out, res, s);
+        else if (nc <= 128) st = batch_pass<E, 4>(g, o, seeds, V, nc, B, c0, X_out, res, s);
+        else if constexpr (MAXC > 128) st = batch_pass<E, 8>(g, o, seeds, V, nc, B, c0, X_out, res, s);
         else st = PR_ERR_INVALID_ARG;
         if (st != PR_OK && st != PR_NOT_CONVERGED) return st;
         if (st == PR_NOT_CONVERGED) all = st;
@@ -691,12 +727,13 @@ static pr_status solve_batched(pr_graph *g, const pr_options *o, int32_t B, cons
 using namespace fpr;
 
 extern "C" pr_status pr_solve_batched(pr_graph *g, const pr_options *o, int32_t B,
-                                      const int32_t *seeds, void *X_out, pr_result *res,
-                                      void *stream)
+                                      const int32_t *seeds, const void *V, void *X_out,
+                                      pr_result *res, void *stream)
 {
     if (res && B > 0) memset(res, 0, sizeof(pr_result) * (size_t)B);
-    if (!g || !o || B < 1 || !seeds || !X_out) {
-        set_error("pr_solve_batched: need a graph, options, B >= 1, seeds and X_out");
+    if (!g || !o || B < 1 || (!seeds == !V) || !X_out) {
+        set_error("pr_solve_batched: need a graph, options, B >= 1, X_out and exactly one of "
+                  "seeds and V");
         return PR_ERR_INVALID_ARG;
     }
     PR_TRY(validate_options(o));
@@ -710,6 +747,8 @@ extern "C" pr_status pr_solve_batched(pr_graph *g, const pr_options *o, int32_t 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     PR_TRY(ensure_batch_items(g, s));
     return o->precision == PR_FP64
-               ? solve_batched<double>(g, o, B, seeds, static_cast<double *>(X_out), res, s)
-               : solve_batched<float>(g, o, B, seeds, static_cast<float *>(X_out), res, s);
+               ? solve_batched<double>(g, o, B, seeds, static_cast<const double *>(V),
+                                       static_cast<double *>(X_out), res, s)
+               : solve_batched<float>(g, o, B, seeds, static_cast<const float *>(V),
+                                      static_cast<float *>(X_out), res, s);
 }

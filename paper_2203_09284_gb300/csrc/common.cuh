@@ -152,7 +152,8 @@ struct pr_graph {
     int num_sms = 0;
     int max_smem = 0;  // opt-in dynamic shared memory per block (bytes)
     int32_t n = 0;
-    int64_t m = 0;
+    int64_t m = 0;     // edges of the graph (after PR_DEDUP)
+    int64_t m_in = 0;  // edges of the input list (pr_graph_create's m)
     int32_t n_dangling = 0;
     fpr::Mem mem;
     std::vector<fpr::Buf *> owned;
@@ -185,7 +186,7 @@ struct pr_graph {
     // per-column state
     int32_t bnhub = -1, bnseg = 0;
     fpr::Buf bseg_start, bseg_cnt, bseg_desc;
-    fpr::Buf bx0, bx1, bpart, bcols;
+    fpr::Buf bx0, bx1, bpart, bcols, btele;
     fpr::SolveState *host_state = nullptr;  // pinned mirror
 
     // reverse mode: the graph with every edge reversed (its in-lists are

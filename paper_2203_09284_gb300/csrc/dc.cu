@@ -216,15 +216,19 @@ __global__ void k_dc_first_e(DCParams q)
     }
 }
 
-// Inner stop, relative to ||r||_1 (measured at R-MAT scale 22: the FP32 forms
-// reach the FP64 threshold in the fewest sweeps with these; the 16-bit
-// forms stop near their storage precision).
+// Inner stop, relative to ||r||_1 (measured at R-MAT scales 22 and 25: the
+// FP32 forms reach the FP64 threshold in the fewest sweeps with these).  The
+// 16-bit forms stop at 1e-2, above their storage floor: an FP16 correction
+// scaled by its L1 bound stalls near 4e-3 of ||r||_1 at scale 25 (its small
+// entries fall into FP16's subnormal range), so a 4e-3 target ran every
+// inner solve into the stall rule (65 inner sweeps, slower than FP64); BF16's
+// 8-bit significand floors at a few 1e-3.
 static double default_eta(pr_precision pr, bool gs)
 {
     switch (pr) {
     case PR_FP32_DC: return gs ? 3e-5 : 1e-5;
-    case PR_FP16_DC: return 4e-3;
-    case PR_BF16_DC: return 3e-2;
+    case PR_FP16_DC: return 1e-2;
+    case PR_BF16_DC: return 1e-2;
     default: return 1e-5;
     }
 }

@@ -478,11 +478,40 @@ static pr_status sort_pairs(pr_graph *g, uint64_t *keys, int32_t *vals, int64_t 
     return st;
 }
 
+// PR_DEDUP: 1 where the sorted (dst, src) key starts a run of equal keys
+// (the run's first entry is the edge's first occurrence: the sort is stable)
+__global__ void k_first_of_run(int64_t m, const uint64_t *__restrict__ keys, int32_t *flag)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+        flag[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+__global__ void k_compact_runs(int64_t m, const uint64_t *__restrict__ keys,
+                               const int32_t *__restrict__ vals, const int32_t *__restrict__ flag,
+                               const int32_t *__restrict__ pos, uint64_t *kout, int32_t *vout)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+        if (flag[i]) {
+            kout[pos[i]] = keys[i];
+            vout[pos[i]] = vals[i];
+        }
+}
+
+// out-degrees of the kept edges (sources in the low 32 bits of the keys)
+__global__ void k_count_sources(int64_t m, const uint64_t *__restrict__ keys, int32_t *outdeg)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+        atomicAdd(&outdeg[(uint32_t)keys[i]], 1);
+}
+
 static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, const float *w,
                            uint32_t flags, cudaStream_t s)
 {
     const int32_t n = g->n;
-    const int64_t m = g->m;
+    int64_t m = g->m;
     const size_t mm = (size_t)std::max<int64_t>(m, 1);
     for (auto pb : {std::make_pair(&g->outdeg, sizeof(int32_t) * (size_t)n),
                     std::make_pair(&g->indeg, sizeof(int32_t) * (size_t)n),
@@ -560,7 +589,42 @@ static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, 
             int32_t *valt = va == eid ? v2.as<int32_t>() : eid;
             st = radix_sort(g, ka, va, kalt, valt, m, digit_shifts(n, 32), s, &kb, &vb);
         }
-        if (st == PR_OK) {
+        if (st == PR_OK && (flags & PR_DEDUP)) {
+            // repeated (src, dst) pairs are adjacent after the sort, first
+            // occurrence first: keep each run's first entry, then count the
+            // out-degrees of what is kept
+            Buf fl, pos;
+            st = buf_alloc(g, fl, sizeof(int32_t) * mm, s);
+            if (st == PR_OK) st = buf_alloc(g, pos, sizeof(int32_t) * (mm + 1), s);
+            uint64_t *kc = kb == k1.as<uint64_t>() ? k2.as<uint64_t>() : k1.as<uint64_t>();
+            int32_t *vc = vb == eid ? v2.as<int32_t>() : eid;
+            if (st == PR_OK) {
+                k_first_of_run<<<rb, 256, 0, s>>>(m, kb, fl.as<int32_t>());
+                note_launch();
+                st = scan_exclusive(g, fl.as<int32_t>(), pos.as<int32_t>(), m, s);
+            }
+            int32_t kept = 0;
+            if (st == PR_OK) {
+                k_compact_runs<<<rb, 256, 0, s>>>(m, kb, vb, fl.as<int32_t>(), pos.as<int32_t>(),
+                                                  kc, vc);
+                note_launch();
+                PR_CUDA(cudaMemcpyAsync(&kept, pos.as<int32_t>() + m, sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, s));
+                PR_CUDA(cudaMemsetAsync(g->outdeg.p, 0, sizeof(int32_t) * (size_t)n, s));
+                PR_CUDA(cudaStreamSynchronize(s));
+                m = kept;
+                g->m = kept;
+                kb = kc;
+                vb = vc;
+                if (m > 0) {
+                    k_count_sources<<<rb, 256, 0, s>>>(m, kb, g->outdeg.as<int32_t>());
+                    note_launch();
+                }
+            }
+            drop_temp(g, fl, s);
+            drop_temp(g, pos, s);
+        }
+        if (st == PR_OK && m > 0) {
             k_run_degrees<<<rb, 256, 0, s>>>(m, kb, 1, g->indeg.as<int32_t>(),
                                              g->row_idx.as<int32_t>());
             note_launch();
@@ -636,12 +700,13 @@ static pr_status build_all(pr_graph *g, const int32_t *src, const int32_t *dst, 
     if ((flags & PR_BUILD_CSR) || w) PR_TRY(ensure_csr(g, s));
     if (w && m > 0) {
         g->weighted = true;
-        for (auto pb : {std::make_pair(&g->w, sizeof(float) * (size_t)m),
+        for (auto pb : {std::make_pair(&g->w, sizeof(float) * (size_t)g->m_in),
                         std::make_pair(&g->rowsum, sizeof(double) * (size_t)n),
                         std::make_pair(&g->p64_csc, sizeof(double) * ((size_t)m + 16)),
                         std::make_pair(&g->p32_csc, sizeof(float) * ((size_t)m + 16))})
             PR_TRY(buf_alloc(g, *pb.first, pb.second, s));
-        PR_CUDA(cudaMemcpyAsync(g->w.p, w, sizeof(float) * (size_t)m, cudaMemcpyDefault, s));
+        PR_CUDA(cudaMemcpyAsync(g->w.p, w, sizeof(float) * (size_t)g->m_in, cudaMemcpyDefault,
+                                s));
         k_rowsum<<<(n + 255) / 256, 256, 0, s>>>(n, g->row_ptr.as<int32_t>(),
                                                  g->csr_eid.as<int32_t>(), g->w.as<float>(),
                                                  g->rowsum.as<double>());
@@ -682,6 +747,10 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
         set_error("pr_graph_create: allocator hooks incomplete");
         return PR_ERR_INVALID_ARG;
     }
+    if (flags & ~(PR_BUILD_CSR | PR_DEDUP)) {
+        set_error("pr_graph_create: unknown flags 0x%x", flags);
+        return PR_ERR_INVALID_ARG;
+    }
     // the edge arrays are read by kernels: device (or managed) memory, or
     // page-locked host memory, which the kernels read over the host link
     // through its device address; pageable host memory is refused
@@ -708,6 +777,7 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
     pr_graph *g = new pr_graph();
     g->n = n;
     g->m = m;
+    g->m_in = m;
     g->mem.stream = s;
     if (alloc) {
         g->mem.hooks = *alloc;

@@ -145,3 +145,44 @@ def test_batched_full_size_s20_sampled():
         assert abs(r64[b].iters - run.iters) <= 1
         assert l1(X64[:, b].cpu().numpy(), run.x) <= 1e-12, b
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_dense_teleport_vectors(s12, precision):
+    """Dense teleport vectors V: every column against the oracle's Jacobi with
+    that teleport (dangling mass along it); one-hot columns of V give exactly
+    the seeds path's result."""
+    import paper_2203_09284_gb300 as fp
+    n, src, dst, og, g = s12
+    B = 6
+    rng = np.random.default_rng(7)
+    V = np.zeros((n, B))
+    V[:, 0] = 1.0 / n                                     # uniform: plain PageRank
+    V[:, 1] = rng.random(n)
+    V[rng.random(n) < 0.9, 2] = 0.0                       # sparse
+    V[:, 2] += (np.arange(n) == 5)
+    V[:, 3:] = rng.random((n, B - 3)) ** 4
+    V /= V.sum(axis=0)
+    dt = np.float64 if precision == "fp64" else np.float32
+    X, res = g.solve_batched(V=dev(V.astype(dt)), threshold=TAU, precision=precision)
+    Xh = X.cpu().numpy()
+    for b in range(B):
+        tele = V[:, b].astype(dt).astype(np.float64)
+        run = oracle.jacobi(og, D, tau=TAU, max_iter=1000, tele=tele / tele.sum(),
+                            dangling_along_tele=True)
+        if precision == "fp64":
+            assert res[b].status == 0 and abs(res[b].iters - run.iters) <= 1
+            assert l1(Xh[:, b], run.x) <= 1e-12, b
+        else:
+            assert l1(Xh[:, b], run.x) <= FP32_BOUND, b
+    seeds = gen.seed_vertices(4, n, seed=2)
+    onehot = np.zeros((n, 4), dt)
+    onehot[seeds, np.arange(4)] = 1
+    Xa, _ = g.solve_batched(dev(seeds), threshold=TAU, precision=precision)
+    Xb, _ = g.solve_batched(V=dev(onehot), threshold=TAU, precision=precision)
+    assert torch.equal(Xa, Xb)
+    bad = onehot.copy()
+    bad[0, 0] = -1
+    with pytest.raises(fp.PageRankError) as e:
+        g.solve_batched(V=dev(bad), precision=precision)
+    assert e.value.status == fp.PR_ERR_INVALID_ARG

@@ -134,3 +134,48 @@ def test_build_from_pinned_host_arrays():
                                   ctypes.byref(out))
     assert st == fp.PR_ERR_INVALID_ARG and not out.value
 
+
+
+def test_build_dedup_keeps_first_occurrences():
+    """PR_DEDUP: the graph of the first occurrence of every (src, dst) pair,
+    bit for bit the oracle's build of that list, with csc_eid giving the kept
+    edges' input positions; its solves equal those of the pre-deduplicated
+    list, and pr_backward gives the dropped repeats a zero gradient."""
+    import paper_2203_09284_gb300 as fp
+    for n, src, dst in (gen.rmat(13, 16, seed=9, dedup=False),
+                        gen.random_digraph(8, 0.6, seed=4, self_loops=True, multi=True)):
+        key = src.astype(np.int64) * n + dst
+        _, first = np.unique(key, return_index=True)
+        keep = np.sort(first)  # input positions of first occurrences, in input order
+        assert len(keep) < len(src)
+        g = graph(n, src, dst, dedup=True)
+        assert g.info()["m"] == len(keep)
+        ex = g.export(csr=True)
+        o = oracle.build_graph(n, src[keep], dst[keep])
+        c = lambda k: ex[k].cpu().numpy()
+        for k in ("outdeg", "indeg", "col_ptr", "row_idx", "row_ptr", "col_idx"):
+            assert np.array_equal(c(k), getattr(o, k)), k
+        assert np.array_equal(c("csc_eid"), keep[o.csc_eid])
+        assert np.array_equal(c("csr_eid"), keep[o.csr_eid])
+        assert np.array_equal(c("inv_outdeg").view(np.uint64), o.inv_outdeg.view(np.uint64))
+        n2o, rcol, rrow, _ = oracle.relabel(o)
+        assert np.array_equal(c("new_to_old"), n2o)
+        assert np.array_equal(c("rrow_idx"), rrow)
+        g2 = graph(n, src[keep], dst[keep])
+        x1, _ = g.solve(threshold=1e-12)
+        x2, _ = g2.solve(threshold=1e-12)
+        assert torch.equal(x1, x2)
+        gx = torch.zeros(n, dtype=torch.float64, device="cuda")
+        gx[0] = 1.0
+        gw, gd, _ = g.backward(x1, gx, threshold=1e-13)
+        gw2, gd2, _ = g2.backward(x2, gx, threshold=1e-13)
+        gw = gw.cpu().numpy()
+        assert len(gw) == len(src)
+        drop = np.setdiff1d(np.arange(len(src)), keep)
+        assert (gw[drop] == 0).all()
+        assert np.array_equal(gw[keep], gw2.cpu().numpy())
+        g.close()
+        g2.close()
+    with pytest.raises(fp.PageRankError):
+        fp.pr_graph_create(4, torch.zeros(1, dtype=torch.int32, device="cuda"),
+                           torch.zeros(1, dtype=torch.int32, device="cuda"), flags=4)
