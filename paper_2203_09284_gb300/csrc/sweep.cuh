@@ -499,80 +499,6 @@ struct Src {
     }
 };
 
-// Exact accumulation of gathered doubles without FP64 adds (this part's
-// FP64 pipe adds about 0.5e12 values a second, its integer pipes dozens of
-// times more).  A term v = m 2^(e-1075) (m the 53-bit significand) whose
-// exponent lies in the window [FX_E0, FX_E0 + 64), i.e. 2^-62 <= v < 4, is
-// added exactly into a 128-bit two's-complement integer in units of
-// 2^(FX_E0 - 1075) = 2^-114: its significand shifted left by e - FX_E0.
-// Every other term (zero, subnormal, below 2^-62, 4 or more, negative,
-// non-finite) is added in FP64 to a spill sum.  The integer part is exact
-// and order-free as long as the magnitudes summed into one accumulator stay
-// below 2^13 (the sweeps' gathered values are probabilities divided by
-// out-degrees, whose sum over any in-list is at most the total rank); the
-// final value rounds once to FP64 (plus the spill), so a vertex's sum is at
-// least as accurate as a sequential FP64 sum and independent of the order.
-constexpr uint32_t FX_E0 = 961;
-struct Fx {
-    uint32_t w0, w1, w2, w3;
-    double spill;
-};
-__device__ __forceinline__ Fx fx_zero()
-{
-    Fx f;
-    f.w0 = f.w1 = f.w2 = f.w3 = 0u;
-    f.spill = 0.0;
-    return f;
-}
-__device__ __forceinline__ void fx_add4(Fx &a, uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3)
-{
-    asm("add.cc.u32 %0, %0, %4;\n\t"
-        "addc.cc.u32 %1, %1, %5;\n\t"
-        "addc.cc.u32 %2, %2, %6;\n\t"
-        "addc.u32 %3, %3, %7;"
-        : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2), "+r"(a.w3)
-        : "r"(b0), "r"(b1), "r"(b2), "r"(b3));
-}
-__device__ __forceinline__ void fx_acc(Fx &a, double v)
-{
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
-    const uint32_t hi = static_cast<uint32_t>(b >> 32), lo = static_cast<uint32_t>(b);
-    const uint32_t t = (hi >> 20) - FX_E0;  // the sign bit puts negatives out of range
-    if (t >= 64u) {
-        if (b << 1) a.spill += v;  // zeros add nothing
-        return;
-    }
-    const uint32_t mh = (hi & 0xfffffu) | 0x100000u;
-    const uint32_t r = t & 31u;
-    const uint32_t p0 = lo << r;
-    const uint32_t p1 = __funnelshift_l(lo, mh, r);
-    const uint32_t p2 = __funnelshift_l(mh, 0u, r);
-    if (t >= 32u) fx_add4(a, 0u, p0, p1, p2);
-    else fx_add4(a, p0, p1, p2, 0u);
-}
-// sum over the G lanes of a group (xor butterfly: every lane gets it)
-template <int G>
-__device__ __forceinline__ void fx_group_sum(Fx &a)
-{
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-        const uint32_t b0 = __shfl_xor_sync(FULL, a.w0, o), b1 = __shfl_xor_sync(FULL, a.w1, o),
-                       b2 = __shfl_xor_sync(FULL, a.w2, o), b3 = __shfl_xor_sync(FULL, a.w3, o);
-        const double bs = __shfl_xor_sync(FULL, a.spill, o);
-        fx_add4(a, b0, b1, b2, b3);
-        if (__double_as_longlong(bs) << 1) a.spill += bs;
-    }
-}
-__device__ __forceinline__ double fx_to_double(const Fx &a)
-{
-    const long long hi = static_cast<long long>((static_cast<unsigned long long>(a.w3) << 32) | a.w2);
-    const unsigned long long lo = (static_cast<unsigned long long>(a.w1) << 32) | a.w0;
-    return fma(static_cast<double>(hi), 0x1p-50, static_cast<double>(lo) * 0x1p-114) + a.spill;
-}
-// FP64 unweighted sweeps gather into Fx; the others add in their own type
-template <typename T, typename A, bool W>
-constexpr bool kExact = std::is_same_v<T, double> && std::is_same_v<A, double> && !W;
-
 // This lane's share of the sum over in-list slots [a, e) when G lanes (gl =
 // lane index among them) stream one list: 16-byte index loads, two of them
 // (eight gathers) in flight per lane.
@@ -613,37 +539,6 @@ __device__ __forceinline__ A group_stream(const SweepParams &p, const Src<T, GS>
     return acc;
 }
 
-// group_stream for FP64 unweighted sweeps, into an exact accumulator
-template <int G, bool GS>
-__device__ __forceinline__ Fx group_stream_fx(const SweepParams &p, const Src<double, GS> &src,
-                                              int a, int e, int gl)
-{
-    Fx acc = fx_zero();
-    const uint64_t pol = policy_stream();
-    const int4 zero = make_int4(0, 0, 0, 0);
-    int j0 = (a & ~3) + 4 * gl;
-    int4 q0 = j0 < e ? ld_idx4(p.row_idx + j0, pol) : zero;
-    int4 q1 = j0 + 4 * G < e ? ld_idx4(p.row_idx + j0 + 4 * G, pol) : zero;
-    for (; j0 < e; j0 += 8 * G) {
-        const int j1 = j0 + 4 * G;
-        const int n0 = j0 + 8 * G, n1 = n0 + 4 * G;
-        const int4 r0 = n0 < e ? ld_idx4(p.row_idx + n0, pol) : zero;
-        const int4 r1 = n1 < e ? ld_idx4(p.row_idx + n1, pol) : zero;
-        const int v[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-        double got[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int s = (c < 4 ? j0 : j1) + (c & 3);
-            got[c] = (s >= a && s < e) ? src(v[c]) : 0.0;
-        }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) fx_acc(acc, got[c]);
-        q0 = r0;
-        q1 = r1;
-    }
-    return acc;
-}
-
 template <int G, typename A>
 __device__ __forceinline__ A group_sum(A v)
 {
@@ -666,15 +561,8 @@ __device__ __forceinline__ void hub_item(const SweepParams &p, int i, const int4
     const int h = d.x;
     bool sk = false;
     if constexpr (perf_of<Fin>::value) sk = fin.skip(h, __ldg(p.outdeg + h), ld_y<T, GS>(src.y, h));
-    double s;
-    if constexpr (kExact<T, A, W>) {
-        Fx f = sk ? fx_zero() : group_stream_fx<32, GS>(p, src, d.z, d.w, lane);
-        fx_group_sum<32>(f);
-        s = lane == 0 ? fx_to_double(f) : 0.0;
-    } else {
-        A acc = sk ? A(0) : group_stream<32, T, A, GS, W>(p, src, d.z, d.w, lane);
-        s = warp_sum(static_cast<double>(acc));
-    }
+    A acc = sk ? A(0) : group_stream<32, T, A, GS, W>(p, src, d.z, d.w, lane);
+    const double s = warp_sum(static_cast<double>(acc));
     if (lane == 0) {
         if constexpr (perf_of<Fin>::value) {
             if (!sk) fin.gath += (unsigned long long)(d.w - d.z);
@@ -727,15 +615,8 @@ __device__ __forceinline__ void mid_group(const SweepParams &p, int v0, int v_en
         if (sk) e = a;
         if (act && gl == 0 && !sk) fin.gath += (unsigned long long)(e - a);
     }
-    A acc;
-    if constexpr (kExact<T, A, W>) {
-        Fx f = group_stream_fx<G, GS>(p, src, a, e, gl);
-        fx_group_sum<G>(f);
-        acc = (act && gl == 0) ? fx_to_double(f) : 0.0;
-    } else {
-        acc = group_stream<G, T, A, GS, W>(p, src, a, e, gl);
-        acc = group_sum<G>(acc);
-    }
+    A acc = group_stream<G, T, A, GS, W>(p, src, a, e, gl);
+    acc = group_sum<G>(acc);
     if (act && gl == 0) {
         if (sk) {
             if constexpr (perf_of<Fin>::value) fin.keep(u, od, yo);
@@ -848,13 +729,7 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
             }
             if (!kept) {
                 A acc = 0;
-                if constexpr (kExact<T, A, W>) {
-                    Fx f = fx_zero();
-                    for (int i = a - ea; i < e - ea; ++i) fx_acc(f, vals[i]);
-                    acc = fx_to_double(f);
-                } else {
-                    for (int i = a - ea; i < e - ea; ++i) acc += vals[i];
-                }
+                for (int i = a - ea; i < e - ea; ++i) acc += vals[i];
                 fin(u, acc, od, inv, yo, r);
             }
         }
