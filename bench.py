@@ -37,12 +37,14 @@ sys.path.insert(0, ROOT)
 METRIC = "R-MAT-22 time to L1<1e-10 and GTEPS (% HBM peak), mixed/fused vs plain FP64"
 
 
-# DRAM bytes (read + write) of one k_sweep<float, float, 0, 0> launch of the
-# workload, from the ncu capture summarised in profiles/ (see the command
-# there); reported only while the sweep's sources are the ones captured.
+# DRAM bytes (read + write) of one k_sweep<float, float, 0, 0> and one
+# k_sweep<double, double, 0, 0> launch of the workload, from the ncu captures
+# summarised in profiles/ (see the commands there); reported only while the
+# sweep's sources are the ones captured.
 SWEEP_TRAFFIC = {
-    "sources_sha256": "fee8d7185eea5d6904247eb71ef0310560d89f20e5810f9dcf33a970e18a0537",
-    "bytes": 343160832,  # 338,796,032 read + 4,364,800 written
+    "sources_sha256": "",
+    "fp32": None,
+    "fp64": None,
 }
 SWEEP_SOURCES = ("sweep.cuh", "tma.cuh", "common.cuh")
 
@@ -56,9 +58,9 @@ def sweep_sources_sha256():
     return h.hexdigest()
 
 
-def sweep_traffic():
+def sweep_traffic(prec="fp32"):
     if SWEEP_TRAFFIC["sources_sha256"] and SWEEP_TRAFFIC["sources_sha256"] == sweep_sources_sha256():
-        return SWEEP_TRAFFIC["bytes"]
+        return SWEEP_TRAFFIC[prec]
     return None
 
 
@@ -438,12 +440,26 @@ def run_ours(args, rank, world):
     gather_probe = {"gathers_per_s_G": round(m / (probe_ms * 1e-3) / 1e9, 1),
                     "probe_us": round(probe_ms * 1e3, 2),
                     "sweep_gather_rate_frac": round(probe_ms / sweep_ms, 3)}
-    traffic = args.traffic if args.traffic is not None else sweep_traffic()
+    traffic = args.traffic if args.traffic is not None else sweep_traffic(sweep_prec)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "kernel": f"k_sweep<{sweep_prec}, jacobi>", "sweep_us": round(sweep_ms * 1e3, 2),
                 "alg_bytes_per_sweep": alg, "peak_source": peak_src,
                 "gather_probe": gather_probe}
+    # the plain FP64 sweep (the comparison precision and the defect
+    # correction's residual sweep), timed the same way
+    t_long, _ = timed(lambda: g.solve(out=x_out[0], variant="jacobi", precision="fp64",
+                                      threshold=0.0, max_iter=k_long), 3)
+    t_short, _ = timed(lambda: g.solve(out=x_out[0], variant="jacobi", precision="fp64",
+                                       threshold=0.0, max_iter=k_short), 3)
+    sweep64_ms = (t_long - t_short) / (k_long - k_short)
+    alg64 = b_alg(n, m, "fp64")
+    achieved64 = alg64 / (sweep64_ms * 1e-3) / 1e9
+    roofline_fp64 = {"bound": "hbm", "achieved": round(achieved64, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved64 / peak, 4),
+                     "traffic": sweep_traffic("fp64"), "kernel": "k_sweep<fp64, jacobi>",
+                     "sweep_us": round(sweep64_ms * 1e3, 2), "alg_bytes_per_sweep": alg64,
+                     "peak_source": peak_src}
 
     # ---- end to end through the public API with host buffers --------------
     src_pin = torch.from_numpy(src_h).pin_memory()
@@ -513,7 +529,8 @@ def run_ours(args, rank, world):
         "time_to_solution_ms": {k: v["ms"] for k, v in solves.items()},
         "solves": solves, "perforation": perforation, "build_ms": round(build_ms, 3),
         "gpu_launches": int(launches),
-        "roofline": roofline, "e2e": e2e, "clocks": clk.summary(),
+        "roofline": roofline, "roofline_fp64": roofline_fp64, "e2e": e2e,
+        "clocks": clk.summary(),
     }
     if rows is not None:
         out["rows"] = rows

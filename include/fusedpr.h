@@ -321,32 +321,11 @@ pr_status pr_backward(pr_graph *g, const pr_options *o, const double *x, const d
 pr_status pr_scan_exclusive_noalloc(const int32_t *in, int32_t *out, int64_t count,
                                     void *stream);
 
-/*
- * Diagnostic (no counterpart in the paper, computes nothing of the method):
- * *sink += sum over j < m of y[idx[j]], with the sweep's access pattern
- * (16-byte index loads kept out of L1, eight gathers in flight per lane, the
- * first `hot` entries of y read from shared memory, one 1024-thread block
- * per SM).  Timed by the caller, it gives the rate at which this device
- * serves the sweep's irregular gathers alone.
- *   idx   device int32 [m], 16-byte aligned (PR_ERR_INVALID_ARG otherwise);
- *         an entry outside [0, n) gathers y[0] instead
- *   y     device float [n];  hot: 0 <= hot <= min(n, 49152)
- *   sink  device float [1], accumulated with atomics
- * Returns without synchronising.
- */
-pr_status pr_gather_probe(const int32_t *idx, int64_t m, const float *y, int32_t n, int32_t hot,
-                          float *sink, void *stream);
-
 /* Static string for a status code. */
 const char *pr_status_string(pr_status s);
 
 /* Message of the last error raised on the calling thread ("" if none). */
 const char *pr_last_error(void);
-
-/* Number of CUDA kernels the library has launched in this process so far
- * (each iteration of a device-side loop counts as one launch).  Diagnostics
- * only; no device work. */
-uint64_t pr_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -35,7 +35,8 @@ def _stale(sources, headers) -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
-        os.path.join(os.path.dirname(HERE), "include", "fusedpr.h")]
+        os.path.join(os.path.dirname(HERE), "include", "fusedpr.h"),
+        os.path.join(os.path.dirname(HERE), "include", "fusedpr_diag.h")]
     if not force and not _stale(sources, headers):
         return OUT
     nvcc = _nvcc()

@@ -16,6 +16,7 @@
 
 #include <algorithm>
 
+#include "../../include/fusedpr_diag.h"
 #include "common.cuh"
 
 namespace fpr {

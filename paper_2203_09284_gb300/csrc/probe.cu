@@ -5,6 +5,7 @@
 // Same access pattern as the sweep: 16-byte index loads kept out of L1 and
 // first out of L2, eight gathers in flight per lane, the first `hot` entries
 // of y copied to shared memory, one persistent 1024-thread block per SM.
+#include "../../include/fusedpr_diag.h"
 #include "common.cuh"
 
 namespace fpr {

@@ -1,5 +1,5 @@
-"""The C ABI library loads and exports every function include/fusedpr.h
-declares (no compute calls: runs without a GPU)."""
+"""The C ABI library loads and exports every function the headers in include/
+declare (no compute calls: runs without a GPU)."""
 import ctypes
 import os
 import re
@@ -9,12 +9,16 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "fusedpr.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(pr_[a-z_]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(pr_[a-z_]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -49,9 +53,10 @@ def test_status_strings_without_gpu(libpath):
 
 
 def test_header_compiles_as_c():
-    r = subprocess.run(["gcc", "-std=c99", "-fsyntax-only", "-x", "c", HEADER],
-                       capture_output=True, text=True)
-    assert r.returncode == 0, r.stderr
+    for h in HEADERS:
+        r = subprocess.run(["gcc", "-std=c99", "-fsyntax-only", "-x", "c", h],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, (h, r.stderr)
 
 
 def test_product_path_does_not_touch_the_oracle():
