@@ -273,17 +273,23 @@ pr_status pr_solve_batched(pr_graph *g, const pr_options *o, int32_t B, const in
 
 /*
  * Solves G independent graphs in one sequence of launches (each sweep is one
- * kernel over the work items of every graph that has not converged yet).
- *   graphs  host [G] handles (distinct)
+ * kernel over the work items of every graph that has not converged yet):
+ * Algorithm 1 (PR_JACOBI) or Algorithm 2 / Eq. 9 (PR_FUSED_GS, in place,
+ * rescaled after each sweep unless o->no_rescale) per graph, with each
+ * graph's own stop rule.
+ *   graphs  host [G] handles (distinct, on one device)
  *   x_out   host [G] array of device double pointers, x_out[i] of size n_i
  *   res     host [G], nullable
- * o->variant must be PR_JACOBI and o->precision PR_FP64 or PR_FP32.
+ * o->precision must be PR_FP64 or PR_FP32, o->x0 NULL, no perforation
+ * (PR_ERR_UNSUPPORTED otherwise).
  */
 pr_status pr_solve_multi(pr_graph *const *graphs, int32_t G, const pr_options *o,
                          double *const *x_out, pr_result *res, void *stream);
 
 /*
- * Reverse mode of pr_solve at its fixed point.  Given x (the forward result)
+ * Reverse mode of pr_solve at its fixed point (the paper has no gradients:
+ * this differentiates the fixed point of Eq. 1, x = (1-d)/n + d M x, with
+ * M = P^T + dangling redistribution).  Given x (the forward result)
  * and grad_x = dL/dx, solves the transposed system
  *     (I - d M)^T lambda = grad_x
  * by iteration over the out-lists, then

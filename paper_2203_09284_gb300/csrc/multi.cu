@@ -9,8 +9,10 @@
 // graph and counts the item; the warp that counts a graph's last item closes
 // that graph's sweep (stop test, next scalars).  The block that finishes the
 // launch last keeps the device loop running while any graph is active.
-// Jacobi sweep (Algorithm 1) only: its result does not depend on which warp
-// runs which item.
+// Jacobi (Algorithm 1: the result does not depend on which warp runs which
+// item) or the fused sweep (Algorithm 2 / Eq. 9: each graph's stored vector
+// is updated in place, as the single-graph fused sweep in one launch, and
+// rescaled to sum 1 after each sweep).
 #include <string.h>
 
 #include <algorithm>
@@ -35,21 +37,28 @@ struct MultiParams {
     int32_t use_cond;
 };
 
-template <typename T, typename A, bool W>
+template <typename T, typename A, bool GS, bool W>
 __device__ __forceinline__ void multi_item(const SweepParams &p, int j, int lane,
                                            unsigned char *slice, const Layout &L)
 {
     SolveState *st = p.st;
     const int iter = st->iter;
-    const T *yin = static_cast<const T *>((iter & 1) ? p.y1 : p.y0);
-    T *yout = static_cast<T *>((iter & 1) ? p.y0 : p.y1);
-    SweepFin<T, A, false, W> fin(p, load_ctx<A>(st), yout);
-    const Src<T, false> src{yin, nullptr, 0};
+    const T *yin;
+    T *yout;
+    if constexpr (GS) {
+        yin = static_cast<const T *>(p.y0);
+        yout = static_cast<T *>(p.y0);
+    } else {
+        yin = static_cast<const T *>((iter & 1) ? p.y1 : p.y0);
+        yout = static_cast<T *>((iter & 1) ? p.y0 : p.y1);
+    }
+    SweepFin<T, A, GS, W> fin(p, load_ctx<A>(st), yout);
+    const Src<T, GS> src{yin, nullptr, 0};
     const int nh = p.nhubseg, nm = p.mi[4];
     const int4 d = __ldg(p.desc + j);
-    if (j < nh) hub_item<T, A, false, W>(p, j, d, src, fin, lane);
-    else if (j < nh + nm) mid_item<T, A, false, W>(p, j - nh, d, src, fin, lane);
-    else low_item<T, A, false, W>(p, d, src, fin, lane, slice, L);
+    if (j < nh) hub_item<T, A, GS, W>(p, j, d, src, fin, lane);
+    else if (j < nh + nm) mid_item<T, A, GS, W>(p, j - nh, d, src, fin, lane);
+    else low_item<T, A, GS, W>(p, d, src, fin, lane, slice, L);
     // this item's sums, then the item count; the last item closes the sweep
     const double l1 = warp_sum(static_cast<double>(fin.pt.l1));
     const double lm = warp_max(static_cast<double>(fin.pt.lmax));
@@ -70,7 +79,7 @@ __device__ __forceinline__ void multi_item(const SweepParams &p, int j, int lane
     __syncwarp();
 }
 
-template <typename T, typename A>
+template <typename T, typename A, bool GS>
 __global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_multi_sweep(MultiParams mp)
 {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -97,8 +106,8 @@ __global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_multi_sweep(MultiParam
         const SweepParams &p = mp.params[lo];
         if (*reinterpret_cast<volatile int *>(&p.st->done)) continue;
         const int j = i - __ldg(mp.off + lo);
-        if (p.ew) multi_item<T, A, true>(p, j, lane, slice, L);
-        else multi_item<T, A, false>(p, j, lane, slice, L);
+        if (p.ew) multi_item<T, A, GS, true>(p, j, lane, slice, L);
+        else multi_item<T, A, GS, false>(p, j, lane, slice, L);
     }
     __threadfence();
     __syncthreads();
@@ -123,6 +132,7 @@ static pr_status solve_multi(pr_graph *const *graphs, int32_t G, const pr_option
                              double *const *x_out, pr_result *res, cudaStream_t s)
 {
     constexpr bool fp64 = sizeof(A) == 8;
+    const bool gs = o->variant == PR_FUSED_GS;
     pr_graph *g0 = graphs[0];
     std::vector<SweepParams> hp((size_t)G);
     std::vector<int32_t> off((size_t)G + 1, 0);
@@ -134,6 +144,7 @@ static pr_status solve_multi(pr_graph *const *graphs, int32_t G, const pr_option
         p.stage = 0;
         p.close = 1;
         p.use_cond = 0;
+        p.renorm = (gs && !o->no_rescale) ? 1 : 0;
         lcap = std::max(lcap, p.lcap);
         off[(size_t)k + 1] = off[(size_t)k] + p.nhubseg + p.mi[4] + p.nlt;
         SolveState *hs = g->host_state;
@@ -142,7 +153,8 @@ static pr_status solve_multi(pr_graph *const *graphs, int32_t G, const pr_option
         const int ib = std::max(1, std::min<int>((g->n + 255) / 256, g->num_sms * 8));
         k_init<T, A><<<ib, 256, 0, s>>>(g->n, nullptr, g->n2o.as<int32_t>(),
                                        p.outdeg, static_cast<const A *>(p.inv),
-                                       static_cast<T *>(p.y0), p.st, 0, g->weighted ? 1 : 0);
+                                       static_cast<T *>(p.y0), p.st, p.renorm,
+                                       g->weighted ? 1 : 0);
         note_launch();
     }
     PR_LAUNCH_CHECK();
@@ -165,7 +177,8 @@ static pr_status solve_multi(pr_graph *const *graphs, int32_t G, const pr_option
     mp.off = doff;
     mp.lcap = lcap;
     mp.ms = ms;
-    const void *func = reinterpret_cast<const void *>(&k_multi_sweep<T, A>);
+    const void *func = gs ? reinterpret_cast<const void *>(&k_multi_sweep<T, A, true>)
+                          : reinterpret_cast<const void *>(&k_multi_sweep<T, A, false>);
     const size_t smem = make_layout(lcap, sizeof(A), sizeof(T), false, 0).total;
     const unsigned grid = sweep_grid(g0, off[(size_t)G], func, smem);
     if (grid == 0) return PR_ERR_INVALID_ARG;
@@ -224,7 +237,7 @@ static pr_status solve_multi(pr_graph *const *graphs, int32_t G, const pr_option
         const int ib = std::max(1, std::min<int>((g->n + 255) / 256, g->num_sms * 8));
         k_output<T><<<ib, 256, 0, s>>>(g->n, g->o2n.as<int32_t>(), p.outdeg,
                                        static_cast<const T *>(p.y0), static_cast<const T *>(p.y1),
-                                       1, p.st, x_out[k], g->weighted ? 1 : 0);
+                                       gs ? 0 : 1, p.st, x_out[k], g->weighted ? 1 : 0);
         note_launch();
         PR_LAUNCH_CHECK();
         pr_status st = finish_result(g, res ? &res[k] : nullptr, s, 0);
@@ -249,9 +262,10 @@ extern "C" pr_status pr_solve_multi(pr_graph *const *graphs, int32_t G, const pr
         return PR_ERR_INVALID_ARG;
     }
     PR_TRY(validate_options(o));
-    if (o->variant != PR_JACOBI || (o->precision != PR_FP64 && o->precision != PR_FP32) ||
-        o->x0) {
-        set_error("pr_solve_multi: supports the Jacobi sweep in FP64 or FP32 from x0 = 1/n");
+    if ((o->precision != PR_FP64 && o->precision != PR_FP32) || o->x0 ||
+        o->perforate_eps > 0.0) {
+        set_error("pr_solve_multi: supports the Jacobi and fused sweeps in FP64 or FP32 from "
+                  "x0 = 1/n");
         return PR_ERR_UNSUPPORTED;
     }
     for (int k = 0; k < G; ++k) {

@@ -186,3 +186,23 @@ def test_batched_dense_teleport_vectors(s12, precision):
     with pytest.raises(fp.PageRankError) as e:
         g.solve_batched(V=dev(bad), precision=precision)
     assert e.value.status == fp.PR_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("precision,B", [("fp32", 300), ("fp64", 140)])
+def test_batched_dense_teleport_across_passes(s12, precision, B):
+    """Dense V wider than one pass (256 FP32 / 128 FP64 columns): sampled
+    columns of every pass against the oracle's Jacobi with that teleport."""
+    n, src, dst, og, g = s12
+    rng = np.random.default_rng(B)
+    dt = np.float64 if precision == "fp64" else np.float32
+    V = (rng.random((n, B)) ** 6).astype(dt)
+    V /= V.sum(axis=0, dtype=np.float64).astype(dt)
+    X, res = g.solve_batched(V=dev(V), threshold=TAU, precision=precision)
+    Xh = X.cpu().numpy()
+    for b in sorted({0, 1, 127, 128, 129, 255, 256, B - 1} & set(range(B))):
+        tele = V[:, b].astype(np.float64)
+        run = oracle.jacobi(og, D, tau=TAU, max_iter=1000, tele=tele / tele.sum(),
+                            dangling_along_tele=True)
+        tol = 1e-12 if precision == "fp64" else FP32_BOUND
+        assert l1(Xh[:, b], run.x) <= tol, b
+        assert abs(Xh[:, b].sum() - 1) < (1e-13 if precision == "fp64" else 1e-5)

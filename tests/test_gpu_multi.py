@@ -69,7 +69,31 @@ def test_multi_host_loop_fp32_and_errors(family):
     with pytest.raises(fp.PageRankError):
         fp.solve_multi([gs[0], gs[0]])
     with pytest.raises(fp.PageRankError):
-        fp.solve_multi(gs[:2], variant="gs")
+        fp.solve_multi(gs[:2], precision="fp32_dc")
+    with pytest.raises(fp.PageRankError):
+        fp.solve_multi(gs[:2], perforate_eps=1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_multi_fused_sweep(family, precision):
+    """The fused sweep (Algorithm 2, asynchronous, rescaled) on every graph
+    in one launch per sweep: each result within the stop rule's bound of its
+    graph's fixed point, in no more sweeps than Jacobi; with no_rescale the
+    literal Algorithm 2 reaches the same fixed points."""
+    import paper_2203_09284_gb300 as fp
+    gs, ogs = family
+    tau = 1e-10 if precision == "fp64" else 1e-6
+    xj, rj = fp.solve_multi(gs, threshold=tau, precision=precision)
+    xg, rg = fp.solve_multi(gs, threshold=tau, precision=precision, variant="gs")
+    xl, rl = fp.solve_multi(gs, threshold=tau, precision=precision, variant="gs",
+                            no_rescale=True, max_iter=3000)
+    for (og, csc_p), x, r, a, b, y, c in zip(ogs, xg, rg, xj, rj, xl, rl):
+        assert r.status == 0 and c.status == 0
+        star = oracle.fixed_point(og, D, csc_p=csc_p).x
+        bound = BOUND if precision == "fp64" else 1e-5
+        assert l1(x, star) <= bound
+        assert l1(y, star) <= (1e-9 if precision == "fp64" else 1e-5)
+        assert r.iters <= b.iters + 1
 
 
 def test_multi_64_uneven_graphs():
