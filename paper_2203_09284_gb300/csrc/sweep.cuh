@@ -531,13 +531,7 @@ __device__ __forceinline__ A group_stream(const SweepParams &p, const Src<T, GS>
         for (int c = 0; c < 8; ++c) {
             const int s = (c < 4 ? j0 : j1) + (c & 3);
             if constexpr (W) got[c] = (s >= a && s < e) ? ew[s] * got[c] : A(0);
-            // FP64 adds are this part's scarce unit: a slot past the end of
-            // the list (the padding of a step) adds nothing
-            if constexpr (sizeof(A) == 8) {
-                if (s >= a && s < e) acc += got[c];
-            } else {
-                acc += got[c];
-            }
+            acc += got[c];
         }
         q0 = r0;
         q1 = r1;
