@@ -286,6 +286,15 @@ def measure_rows(dev, stream, peak, timed):
                      "l1_vs_fp64_1e-13": float((x - x_ref).abs().sum())}
     for prec in ("fp32_dc", "bf16_dc", "fp16_dc"):
         row[prec]["speedup_vs_fp64"] = round(row["fp64"]["ms"] / row[prec]["ms"], 3)
+    # the FP32 (134 MB) and FP64 (268 MB) vectors exceed L2 here: the
+    # in-list gather sweep against the propagation-blocked one, per sweep
+    for prec in ("fp32", "fp64"):
+        for name, tune in (("gather", None), ("blocked", {"blocking": 1})):
+            tl, _ = timed(lambda: g.solve(out=x, precision=prec, threshold=0.0, max_iter=9,
+                                          tune=tune), 2)
+            ts, _ = timed(lambda: g.solve(out=x, precision=prec, threshold=0.0, max_iter=1,
+                                          tune=tune), 2)
+            row[f"{prec}_{name}_sweep_ms"] = round((tl - ts) / 8, 3)
     del x_ref
     g.close()
     del x
@@ -402,6 +411,23 @@ def run_ours(args, rank, world):
                                 "status": r.status,
                                 "gathered_sweeps": round(r.gathered / m, 2),
                                 "l1_vs_fp64_1e-13": float((x - x_ref).abs().sum())}
+
+    # propagation-blocked Jacobi (pr_tune.blocking) next to the in-list
+    # gather sweep: per-sweep time (41 minus 1 sweeps) and time to the stop
+    blocked = {}
+    for prec, thr in (("fp64", 1e-10), ("fp32", 1e-6)):
+        row_b = {}
+        for name, tune in (("gather", None), ("blocked", {"blocking": 1})):
+            tl, _ = timed(lambda: g.solve(out=x_out[0], precision=prec, threshold=0.0,
+                                          max_iter=41, tune=tune))
+            ts, _ = timed(lambda: g.solve(out=x_out[0], precision=prec, threshold=0.0,
+                                          max_iter=1, tune=tune))
+            ms, (x, r) = timed(lambda: g.solve(out=x_out[0], precision=prec, threshold=thr,
+                                               tune=tune))
+            row_b[name] = {"sweep_us": round((tl - ts) / 40 * 1e3, 1), "ms": round(ms, 3),
+                           "sweeps": r.iters, "status": r.status,
+                           "l1_vs_fp64_1e-13": float((x - x_ref).abs().sum())}
+        blocked[prec] = row_b
 
     # dominant kernel: the cheap sweep of the headline precision, timed by
     # events around back-to-back launches of the device loop
@@ -527,7 +553,8 @@ def run_ours(args, rank, world):
                    "l2_flush": "inputs larger than L2 (index stream 4E per sweep)",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "time_to_solution_ms": {k: v["ms"] for k, v in solves.items()},
-        "solves": solves, "perforation": perforation, "build_ms": round(build_ms, 3),
+        "solves": solves, "perforation": perforation, "blocked": blocked,
+        "build_ms": round(build_ms, 3),
         "gpu_launches": int(launches),
         "roofline": roofline, "roofline_fp64": roofline_fp64, "e2e": e2e,
         "clocks": clk.summary(),
@@ -607,6 +634,8 @@ def main():
                          "max-norm change of 1e-15 (the paper's stop rule) for both sweeps")
     ap.add_argument("--sweeps", type=int, default=4)
     ap.add_argument("--variant", default="jacobi", choices=["jacobi", "gs"])
+    ap.add_argument("--blocking", action="store_true",
+                    help="sweeps mode: the propagation-blocked Jacobi sweep")
     args = ap.parse_args()
     if args.mode == "sweeps":
         run_sweeps(args)
@@ -653,7 +682,8 @@ def run_sweeps(args):
     dev = torch.device("cuda", 0)
     g = fp.Graph(n, torch.from_numpy(src_h).to(dev), torch.from_numpy(dst_h).to(dev))
     x, r = g.solve(variant=args.variant, precision=args.precision, threshold=0.0,
-                   max_iter=args.sweeps, use_graph=False)
+                   max_iter=args.sweeps, use_graph=False,
+                   tune={"blocking": 1} if args.blocking else None)
     torch.cuda.synchronize()
     print(json.dumps({"mode": "sweeps", "n": n, "edges": len(src_h), "sweeps": r.iters,
                       "outer": r.outer_iters, "precision": args.precision,

@@ -115,6 +115,15 @@ typedef struct {
                           before the second), 2 one.  Changes which values
                           a fused sweep reads fresh, hence its sweep count,
                           not the fixed point. */
+    int32_t blocking;  /* 1: Jacobi sweeps (PR_FP64 / PR_FP32, unweighted, no
+                          perforation) run propagation-blocked: contributions
+                          scattered into bins of 16384 destinations, then
+                          summed per bin in shared memory (the locality
+                          technique the paper's related work cites for
+                          vectors that do not fit in cache; built on first
+                          use, about 20 bytes per edge).  Sums are added with
+                          atomics, so results vary at rounding level.  0
+                          (default): the in-list gather sweep. */
 } pr_tune;
 
 typedef struct {

@@ -229,6 +229,7 @@ pr_tune effective_tune(const pr_graph *g, const pr_tune *t)
         r.deterministic_gs = t->deterministic_gs;
         r.wait_limit = t->wait_limit > 0 ? t->wait_limit : 0;
         r.fused_split = t->fused_split;
+        r.blocking = t->blocking ? 1 : 0;
     }
     r.fused_split = std::max(0, std::min(r.fused_split, 2));
     r.stage_kb = r.stage_kb < 0 ? -1 : std::min(r.stage_kb, 227);
@@ -459,6 +460,7 @@ static void destroy_impl(pr_graph *g)
     g->rev = nullptr;
     release_graphs(g);
     for (Buf *b : g->owned) buf_free(g, *b, s);
+    release_blocked(g);
     cudaStreamSynchronize(s);
     if (g->host_state) cudaFreeHost(g->host_state);
     cudaGetLastError();

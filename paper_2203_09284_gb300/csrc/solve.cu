@@ -464,6 +464,7 @@ extern "C" pr_status pr_solve(pr_graph *g, const pr_options *o, double *x_out, p
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     pr_tune tn;
     PR_TRY(prepare_solve(g, o, tn, s));
+    if (tn.blocking) return solve_blocked(g, o, x_out, res, s);
     if (o->perforate_eps > 0.0 && o->precision != PR_FP64 && o->precision != PR_FP32) {
         set_error("loop perforation needs PR_FP64 or PR_FP32");
         return PR_ERR_UNSUPPORTED;

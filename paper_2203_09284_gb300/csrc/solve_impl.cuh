@@ -59,5 +59,8 @@ void init_state(pr_graph *g, const pr_options *o, SolveState &h);
 pr_status finish_result(pr_graph *g, pr_result *res, cudaStream_t s, int outer);
 pr_status solve_dc(pr_graph *g, const pr_options *o, const pr_tune &tn, double *x_out,
                    pr_result *res, cudaStream_t s);
+// propagation-blocked Jacobi (blocked.cu)
+pr_status solve_blocked(pr_graph *g, const pr_options *o, double *x_out, pr_result *res,
+                        cudaStream_t s);
 
 }  // namespace fpr
