@@ -22,6 +22,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "solve_impl.cuh"
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(PB_BS) k_pb_accumulate(const SolveState *st, i
 }
 
 template <typename T, typename A>
-__global__ void k_pb_epilogue(SweepParams p, A *gacc)
+__global__ void __launch_bounds__(PB_BS) k_pb_epilogue(SweepParams p, A *gacc)
 {
     SolveState *st = p.st;
     if (st->done) {
@@ -139,6 +141,19 @@ __global__ void k_pb_epilogue(SweepParams p, A *gacc)
 }
 
 // ---------------------------------------------------------------- build
+// Each graph's layout, built on its first blocked solve (its buffers are
+// owned by the graph and freed with it; the record goes at destroy).
+static std::mutex pb_mu;
+static std::unordered_map<const pr_graph *, PbLayout *> pb_layouts;
+
+static PbLayout &layout_of_graph(pr_graph *g)
+{
+    std::lock_guard<std::mutex> lk(pb_mu);
+    PbLayout *&L = pb_layouts[g];
+    if (!L) L = new PbLayout();
+    return *L;
+}
+
 static void *tmp_alloc(pr_graph *g, size_t bytes, cudaStream_t s)
 {
     return g->mem.alloc(bytes ? bytes : 16, s);
@@ -146,8 +161,7 @@ static void *tmp_alloc(pr_graph *g, size_t bytes, cudaStream_t s)
 
 static pr_status ensure_blocked(pr_graph *g, cudaStream_t s)
 {
-    if (!g->pb) g->pb = new PbLayout();
-    PbLayout &L = *g->pb;
+    PbLayout &L = layout_of_graph(g);
     if (L.val.p && L.m == g->m) return PR_OK;
     const int32_t n = g->n;
     const int64_t m = g->m;
@@ -237,8 +251,11 @@ static pr_status ensure_blocked(pr_graph *g, cudaStream_t s)
 
 void release_blocked(pr_graph *g)
 {
-    delete g->pb;
-    g->pb = nullptr;
+    std::lock_guard<std::mutex> lk(pb_mu);
+    auto it = pb_layouts.find(g);
+    if (it == pb_layouts.end()) return;
+    delete it->second;
+    pb_layouts.erase(it);
 }
 
 // ---------------------------------------------------------------- solve
@@ -248,7 +265,7 @@ static pr_status solve_blocked_t(pr_graph *g, const pr_options *o, double *x_out
 {
     constexpr bool fp64 = sizeof(A) == 8;
     PR_TRY(ensure_blocked(g, s));
-    PbLayout &L = *g->pb;
+    PbLayout &L = layout_of_graph(g);
     SweepParams p;
     fill_params(g, p, fp64, sizeof(T), false);
     p.renorm = 0;
@@ -271,7 +288,9 @@ static pr_status solve_blocked_t(pr_graph *g, const pr_options *o, double *x_out
     const unsigned g_sc = (unsigned)std::max<int64_t>(1, std::min<int64_t>((L.m + 255) / 256,
                                                                          (int64_t)g->num_sms * 16));
     const unsigned g_ac = (unsigned)std::max(1, std::min(L.nunits, g->num_sms * 2));
-    const unsigned g_ep = (unsigned)std::max(1, std::min((n + 255) / 256, g->num_sms * 8));
+    // one block per SM: the per-block partial sums and the closing ticket
+    // are a few hundred atomics, not thousands
+    const unsigned g_ep = (unsigned)std::max(1, std::min((n + PB_BS - 1) / PB_BS, g->num_sms));
     const SolveState *cst = p.st;
     int64_t mloc = L.m;
     const int32_t *csrc = L.csrc.as<int32_t>(), *pos = L.pos.as<int32_t>();
@@ -318,7 +337,7 @@ static pr_status solve_blocked_t(pr_graph *g, const pr_options *o, double *x_out
             k2.kernelParams = a_ac;
             k3.func = const_cast<void *>(f_ep);
             k3.gridDim = dim3(g_ep);
-            k3.blockDim = dim3(256);
+            k3.blockDim = dim3(PB_BS);
             k3.kernelParams = a_ep;
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &k1);
@@ -347,7 +366,7 @@ static pr_status solve_blocked_t(pr_graph *g, const pr_options *o, double *x_out
             for (int k = 0; k < batch; ++k) {
                 PR_CUDA(cudaLaunchKernel(f_sc, dim3(g_sc), dim3(256), a_sc, 0, s));
                 PR_CUDA(cudaLaunchKernel(f_ac, dim3(g_ac), dim3(PB_BS), a_ac, smem_ac, s));
-                PR_CUDA(cudaLaunchKernel(f_ep, dim3(g_ep), dim3(256), a_ep, 0, s));
+                PR_CUDA(cudaLaunchKernel(f_ep, dim3(g_ep), dim3(PB_BS), a_ep, 0, s));
                 note_launch(3);
             }
             launched += batch;

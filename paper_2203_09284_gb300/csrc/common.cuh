@@ -144,8 +144,6 @@ struct Items {
                                   // vertices [v0, v1), in-list slots [ea, eb)
 };
 
-struct PbLayout;  // blocked sweep's layout (blocked.cu)
-
 }  // namespace fpr
 
 // Opaque handle of the C ABI.
@@ -182,7 +180,6 @@ struct pr_graph {
     fpr::Buf state;     // SolveState
     fpr::Buf aux;       // scratch for batched / multi / adjoint
     fpr::Buf lastbuf;   // perforated solves: last change per vertex
-    fpr::PbLayout *pb = nullptr;  // blocked sweep (built on first use)
 
     // batched personalised PageRank: hub segments of the row gather
     // (vertices [0, bnhub) with more than BATCH_SEG in-edges), iterates and
@@ -216,7 +213,6 @@ pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s);
 pr_status ensure_csr(pr_graph *g, cudaStream_t s);
 pr_tune effective_tune(const pr_graph *g, const pr_tune *t);
 int test_stall_requested();
-void release_blocked(pr_graph *g);
 void release_graphs(pr_graph *g);
 
 // exclusive scan of `count` int32 values; out[count] receives the total.

@@ -242,6 +242,9 @@ pr_tune effective_tune(const pr_graph *g, const pr_tune *t)
     return r;
 }
 
+// the blocked sweep's layout of a graph (blocked.cu), released at destroy
+void release_blocked(pr_graph *g);
+
 // Fault-injection hook for the tests of the bounded device waits (not part
 // of the C ABI): with FUSEDPR_TEST_STALL=1 in the environment, every sweep
 // block's first wait also waits on a barrier nothing arrives at, so the wait
