@@ -154,10 +154,23 @@ static PbLayout &layout_of_graph(pr_graph *g)
     return *L;
 }
 
-static void *tmp_alloc(pr_graph *g, size_t bytes, cudaStream_t s)
-{
-    return g->mem.alloc(bytes ? bytes : 16, s);
-}
+// device scratch of the layout build, freed on every return path
+struct TempDev {
+    pr_graph *g;
+    cudaStream_t s;
+    size_t bytes;
+    void *p;
+    TempDev(pr_graph *g_, size_t b, cudaStream_t s_) : g(g_), s(s_), bytes(b ? b : 16)
+    {
+        p = g->mem.alloc(bytes, s);
+    }
+    ~TempDev()
+    {
+        if (p) g->mem.free(p, bytes, s);
+    }
+    template <typename T>
+    T *as() const { return static_cast<T *>(p); }
+};
 
 static pr_status ensure_blocked(pr_graph *g, cudaStream_t s)
 {
@@ -166,7 +179,7 @@ static pr_status ensure_blocked(pr_graph *g, cudaStream_t s)
     const int32_t n = g->n;
     const int64_t m = g->m;
     const size_t mm = (size_t)std::max<int64_t>(m, 1);
-    L.m = m;
+    L.m = -1;  // set once the layout is complete
     L.nbins = (n + PB_BIN - 1) / PB_BIN;
     PR_TRY(buf_alloc(g, L.csrc, sizeof(int32_t) * mm, s));
     PR_TRY(buf_alloc(g, L.pos, sizeof(int32_t) * mm, s));
@@ -176,10 +189,10 @@ static pr_status ensure_blocked(pr_graph *g, cudaStream_t s)
     PR_CUDA(cudaMemsetAsync(L.gacc.p, 0, sizeof(double) * (size_t)L.nbins * PB_BIN, s));
     std::vector<int4> units;
     if (m > 0) {
-        uint64_t *ka = static_cast<uint64_t *>(tmp_alloc(g, sizeof(uint64_t) * mm, s));
-        uint64_t *kb = static_cast<uint64_t *>(tmp_alloc(g, sizeof(uint64_t) * mm, s));
-        int32_t *vb = static_cast<int32_t *>(tmp_alloc(g, sizeof(int32_t) * mm, s));
-        int32_t *bins = static_cast<int32_t *>(tmp_alloc(g, sizeof(int32_t) * (L.nbins + 1), s));
+        TempDev tka(g, sizeof(uint64_t) * mm, s), tkb(g, sizeof(uint64_t) * mm, s);
+        TempDev tvb(g, sizeof(int32_t) * mm, s), tbins(g, sizeof(int32_t) * (L.nbins + 1), s);
+        uint64_t *ka = tka.as<uint64_t>(), *kb = tkb.as<uint64_t>();
+        int32_t *vb = tvb.as<int32_t>(), *bins = tbins.as<int32_t>();
         pr_status st = (ka && kb && vb && bins) ? PR_OK : PR_ERR_OOM;
         if (st != PR_OK) set_error("device allocation for the blocked layout failed");
         uint64_t *kr = nullptr;
@@ -226,10 +239,6 @@ static pr_status ensure_blocked(pr_graph *g, cudaStream_t s)
                                     cudaMemcpyDeviceToHost, s));
             PR_CUDA(cudaStreamSynchronize(s));
         }
-        g->mem.free(ka, sizeof(uint64_t) * mm, s);
-        g->mem.free(kb, sizeof(uint64_t) * mm, s);
-        g->mem.free(vb, sizeof(int32_t) * mm, s);
-        g->mem.free(bins, sizeof(int32_t) * (L.nbins + 1), s);
         PR_TRY(st);
         int64_t start = 0;
         for (int b = 0; b < L.nbins; ++b) {
@@ -246,6 +255,7 @@ static pr_status ensure_blocked(pr_graph *g, cudaStream_t s)
                                 cudaMemcpyHostToDevice, s));
     PR_CUDA(cudaStreamSynchronize(s));
     PR_LAUNCH_CHECK();
+    L.m = m;
     return PR_OK;
 }
 
