@@ -179,3 +179,26 @@ def test_build_dedup_keeps_first_occurrences():
     with pytest.raises(fp.PageRankError):
         fp.pr_graph_create(4, torch.zeros(1, dtype=torch.int32, device="cuda"),
                            torch.zeros(1, dtype=torch.int32, device="cuda"), flags=4)
+
+
+def test_build_dedup_weighted():
+    """PR_DEDUP with edge weights: the kept edges' weights (first
+    occurrences) define P; the solve equals the weighted solve of the
+    deduplicated list, and the oracle's weighted fixed point."""
+    n, src, dst = gen.rmat(12, 16, seed=4, dedup=False)
+    w = gen.edge_weights(len(src), seed=5)
+    key = src.astype(np.int64) * n + dst
+    _, first = np.unique(key, return_index=True)
+    keep = np.sort(first)
+    assert len(keep) < len(src)
+    g = graph(n, src, dst, w=w, dedup=True)
+    g2 = graph(n, src[keep], dst[keep], w=w[keep])
+    x1, r1 = g.solve(threshold=1e-13)
+    x2, r2 = g2.solve(threshold=1e-13)
+    assert torch.equal(x1, x2)
+    og = oracle.build_graph(n, src[keep], dst[keep])
+    _, _, csc_p = oracle.row_normalize(og, w[keep])
+    star = oracle.fixed_point(og, 0.85, csc_p=csc_p)
+    assert float(np.abs(x1.cpu().numpy() - star.x).sum()) <= 0.85 / 0.15 * 1e-13 * 1.01
+    g.close()
+    g2.close()

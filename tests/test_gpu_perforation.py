@@ -4,6 +4,7 @@ same skip decisions (the count of gathered in-list entries is equal), the
 same iterates to rounding, the stop rule's bound when only full sweeps stop,
 and the unsupported combinations refused."""
 import numpy as np
+import torch
 import pytest
 
 import gen
@@ -97,3 +98,12 @@ def test_perforation_degenerate_graphs():
             else:       # approximate: a kept vertex is off by about eps times its value
                 assert (err <= 1e-5 * want).all(), (n, period)
         g.close()
+
+
+def test_perforated_host_loop_matches_graph_loop(s16):
+    """The host-driven loop (use_graph = 0) runs the same perforated sweeps."""
+    n, src, dst, og, g = s16
+    xa, ra = g.solve(threshold=1e-10, perforate_eps=1e-8, perforate_period=4)
+    xb, rb = g.solve(threshold=1e-10, perforate_eps=1e-8, perforate_period=4, use_graph=False)
+    assert ra.iters == rb.iters and ra.gathered == rb.gathered
+    assert torch.equal(xa, xb)
