@@ -42,9 +42,9 @@ METRIC = "R-MAT-22 time to L1<1e-10 and GTEPS (% HBM peak), mixed/fused vs plain
 # summarised in profiles/ (see the commands there); reported only while the
 # sweep's sources are the ones captured.
 SWEEP_TRAFFIC = {
-    "sources_sha256": "7d69d22592ee010d9507e860df306af41a7926e5cc0460eb0ca78110de66868f",
-    "fp32": 342990080,  # 338,820,608 read + 4,169,472 written
-    "fp64": 396217600,  # 377,664,768 read + 18,552,832 written
+    "sources_sha256": "319d1a615b5ca039f7cb6db8cda5e377d5849a72e316872d8e16794662c66387",
+    "fp32": 341392896,  # 337,219,584 read + 4,173,312 written
+    "fp64": 393987328,  # 376,306,944 read + 17,680,384 written
 }
 SWEEP_SOURCES = ("sweep.cuh", "tma.cuh", "common.cuh")
 

@@ -115,6 +115,10 @@ typedef struct {
                           before the second), 2 one.  Changes which values
                           a fused sweep reads fresh, hence its sweep count,
                           not the fixed point. */
+    int32_t mid_wide;  /* mid vertices (t_lo < in-degree <= t_hub) get 32
+                          lanes above mid_wide in-edges, 16 above
+                          mid_wide / 2, 8 above mid_wide / 4 and 4 below
+                          (default 1024; 16 to 2^20) */
     int32_t blocking;  /* 1: Jacobi sweeps (PR_FP64 / PR_FP32, unweighted, no
                           perforation) run propagation-blocked: contributions
                           scattered into bins of 16384 destinations, then

@@ -46,7 +46,8 @@ class PrTune(ctypes.Structure):
     _fields_ = [("t_lo", ctypes.c_int32), ("t_hub", ctypes.c_int32), ("hub_seg", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("deterministic_gs", ctypes.c_int32),
                 ("stage_kb", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
-                ("fused_split", ctypes.c_int32), ("blocking", ctypes.c_int32)]
+                ("fused_split", ctypes.c_int32), ("mid_wide", ctypes.c_int32),
+                ("blocking", ctypes.c_int32)]
 
 
 class PrOptions(ctypes.Structure):

@@ -117,12 +117,13 @@ struct SolveState {
 //                                 in-edges, one warp each
 //   mid   [nhub, nhub + nmid)     t_lo < in-degree <= t_hub: four sub-ranges
 //                                 [mb[k], mb[k+1]) of 32 >> k lanes per vertex
-//                                 (in-degree > 128, > 64, > 32, the rest)
+//                                 (in-degree > mid_wide, > mid_wide / 2,
+//                                 > mid_wide / 4, the rest)
 //   low   [nhub + nmid, n)        in-degree <= t_lo: tiles of consecutive
 //                                 vertices with at most tile_c units of work
 //                                 (in-edges + vertices), one warp each
 struct Items {
-    int32_t t_lo = -1, t_hub = -1, hub_seg = 0, tile_c = 0;
+    int32_t t_lo = -1, t_hub = -1, hub_seg = 0, tile_c = 0, mid_wide = 0;
     int32_t nhub = 0, nmid = 0, nlow = 0;
     int32_t nhubseg = 0;          // hub segments
     int32_t mb[5] = {0, 0, 0, 0, 0};  // mid sub-range bounds

@@ -133,14 +133,15 @@ __global__ void k_relabel_lists(int64_t m, int64_t nchunks, const int32_t *__res
 // counts[0]: in-degree > t_hub; counts[1]: t_lo < in-degree <= t_hub;
 // counts[2..4]: of those, in-degree > max(t_lo, 128 / 64 / 32).
 __global__ void k_count_classes(int32_t n, const int32_t *__restrict__ col_ptr, int t_lo,
-                                int t_hub, int32_t *counts)
+                                int t_hub, int w32, int32_t *counts)
 {
     int u = blockIdx.x * blockDim.x + threadIdx.x;
     int deg = u < n ? col_ptr[u + 1] - col_ptr[u] : -1;
     const bool mid = deg > t_lo && deg <= t_hub;
     unsigned b[5] = {__ballot_sync(FULL, deg > t_hub), __ballot_sync(FULL, mid),
-                     __ballot_sync(FULL, mid && deg > 128), __ballot_sync(FULL, mid && deg > 64),
-                     __ballot_sync(FULL, mid && deg > 32)};
+                     __ballot_sync(FULL, mid && deg > w32),
+                     __ballot_sync(FULL, mid && deg > w32 / 2),
+                     __ballot_sync(FULL, mid && deg > w32 / 4)};
     if ((threadIdx.x & 31) == 0)
         for (int k = 0; k < 5; ++k)
             if (b[k]) atomicAdd(&counts[k], __popc(b[k]));
@@ -230,7 +231,9 @@ pr_tune effective_tune(const pr_graph *g, const pr_tune *t)
         r.wait_limit = t->wait_limit > 0 ? t->wait_limit : 0;
         r.fused_split = t->fused_split;
         r.blocking = t->blocking ? 1 : 0;
+        if (t->mid_wide > 0) r.mid_wide = t->mid_wide;
     }
+    r.mid_wide = std::max(16, std::min(r.mid_wide, 1 << 20));
     r.fused_split = std::max(0, std::min(r.fused_split, 2));
     r.stage_kb = r.stage_kb < 0 ? -1 : std::min(r.stage_kb, 227);
     // a low tile's in-edges (at most tile + t_lo) sit in one warp's slice of
@@ -293,14 +296,15 @@ pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
     it.test_stall = test_stall_requested();
     it.fused_split = t.fused_split;
     if (it.t_lo == t.t_lo && it.t_hub == t.t_hub && it.hub_seg == t.hub_seg &&
-        it.tile_c == t.tile)
+        it.tile_c == t.tile && it.mid_wide == t.mid_wide)
         return PR_OK;
     const int32_t n = g->n;
     const int32_t *rcp = g->r_col_ptr.as<int32_t>();
     Scratch tmp(g, s);
     PR_TRY(tmp.alloc(sizeof(int32_t) * 8));
     PR_CUDA(cudaMemsetAsync(tmp.b.p, 0, sizeof(int32_t) * 8, s));
-    k_count_classes<<<(n + 255) / 256, 256, 0, s>>>(n, rcp, t.t_lo, t.t_hub, tmp.as<int32_t>());
+    k_count_classes<<<(n + 255) / 256, 256, 0, s>>>(n, rcp, t.t_lo, t.t_hub, t.mid_wide,
+                                                      tmp.as<int32_t>());
     note_launch();
     PR_LAUNCH_CHECK();
     int32_t h[8];
@@ -372,6 +376,7 @@ pr_status ensure_items(pr_graph *g, const pr_tune &t, cudaStream_t s)
     it.t_hub = t.t_hub;
     it.hub_seg = t.hub_seg;
     it.tile_c = t.tile;
+    it.mid_wide = t.mid_wide;
     PR_CUDA(cudaStreamSynchronize(s));
     return PR_OK;
 }
@@ -796,6 +801,7 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
     g->tune.deterministic_gs = 0;
     g->tune.stage_kb = 64;
     g->tune.wait_limit = 0;
+    g->tune.mid_wide = 1024;
     pr_status st = PR_OK;
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess)

@@ -425,7 +425,8 @@ pr_status prepare_solve(pr_graph *g, const pr_options *o, pr_tune &tn, cudaStrea
     const Items &it = g->items;
     if (it.t_lo != tn.t_lo || it.t_hub != tn.t_hub || it.hub_seg != tn.hub_seg ||
         it.tile_c != tn.tile || it.stage_kb != tn.stage_kb || it.wait_limit != tn.wait_limit ||
-        it.test_stall != test_stall_requested() || it.fused_split != tn.fused_split)
+        it.test_stall != test_stall_requested() || it.fused_split != tn.fused_split ||
+        it.mid_wide != tn.mid_wide)
         release_graphs(g);  // cached loops hold the old launch parameters
     PR_TRY(ensure_items(g, tn, s));
     PR_TRY(ensure_workspace(g, s));

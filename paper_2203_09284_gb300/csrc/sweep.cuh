@@ -32,8 +32,9 @@
 //                a hub's last segment adds the segment sums in order and
 //                updates the hub
 //   mid group    32/G consecutive mid vertices, G lanes per vertex (G = 32,
-//                16, 8 or 4 as the in-degree falls: more than 128, 64, 32,
-//                else), same streaming gather, then a G-lane reduction
+//                16, 8 or 4 as the in-degree falls: more than mid_wide,
+//                mid_wide/2, mid_wide/4, else; by default 1024, 512, 256),
+//                same streaming gather, then a G-lane reduction
 //   low tile     consecutive low-degree vertices with at most `tile` units of
 //                work: the warp gathers all their in-edges into its slice of
 //                shared memory, then one lane per vertex adds its own

@@ -11,11 +11,11 @@ import json
 import os
 from itertools import product
 
-# (t_lo, t_hub, hub_seg, tile, stage_kb)
+# (t_lo, t_hub, hub_seg, tile, stage_kb, mid_wide)
 DEFAULT_CANDIDATES = [
-    dict(t_lo=t_lo, t_hub=t_hub, hub_seg=seg, tile=tile, stage_kb=stage)
-    for t_lo, (t_hub, seg), tile, stage in product(
-        (16, 32), ((1024, 2048), (4096, 4096)), (128, 256), (32, 64))
+    dict(t_lo=t_lo, t_hub=t_hub, hub_seg=seg, tile=tile, stage_kb=stage, mid_wide=wide)
+    for t_lo, (t_hub, seg), tile, stage, wide in product(
+        (16, 32), ((1024, 2048), (4096, 4096)), (128, 256), (32, 64), (256, 1024))
 ]
 
 

@@ -14,8 +14,8 @@ def test_search_picks_the_fastest_first_on_ties():
 
 def test_default_candidates_are_distinct_and_complete():
     keys = {tuple(sorted(c.items())) for c in tune.DEFAULT_CANDIDATES}
-    assert len(keys) == len(tune.DEFAULT_CANDIDATES) == 16
-    assert all(set(c) == {"t_lo", "t_hub", "hub_seg", "tile", "stage_kb"}
+    assert len(keys) == len(tune.DEFAULT_CANDIDATES) == 32
+    assert all(set(c) == {"t_lo", "t_hub", "hub_seg", "tile", "stage_kb", "mid_wide"}
                for c in tune.DEFAULT_CANDIDATES)
 
 
