@@ -636,6 +636,32 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
 {
     const int v0 = d.x, v1 = d.y, ea = d.z, eb = d.w;
     constexpr bool PF = perf_of<Fin>::value;
+    if (!PF && ea == eb) {
+        // a tile of vertices without in-edges (the tail of the degree-ordered
+        // ids): nothing to gather and no offsets to read; two rounds of
+        // vertex inputs in flight at a time
+        for (int u0 = v0; u0 < v1; u0 += 64) {
+            const int ua = u0 + lane, ub = ua + 32;
+            int oda = 0, odb = 0;
+            A inva = 0, invb = 0, ra = 0, rb = 0;
+            T ya{}, yb{};
+            if (ua < v1) {
+                oda = __ldg(p.outdeg + ua);
+                inva = __ldg(static_cast<const A *>(p.inv) + ua);
+                ya = ld_y<T, GS>(src.y, ua);
+                ra = rhs_of<A>(p, ua, fin.base());
+            }
+            if (ub < v1) {
+                odb = __ldg(p.outdeg + ub);
+                invb = __ldg(static_cast<const A *>(p.inv) + ub);
+                yb = ld_y<T, GS>(src.y, ub);
+                rb = rhs_of<A>(p, ub, fin.base());
+            }
+            if (ua < v1) fin(ua, A(0), oda, inva, ya, ra);
+            if (ub < v1) fin(ub, A(0), odb, invb, yb, rb);
+        }
+        return;
+    }
     A *vals = reinterpret_cast<A *>(slice);
     uint32_t *mask = reinterpret_cast<uint32_t *>(slice + L.wmask);
     const A *ew = static_cast<const A *>(p.ew);
