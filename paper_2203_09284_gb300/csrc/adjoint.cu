@@ -86,7 +86,10 @@ struct AdjFin {
     T *yout;
     Part<A> pt;
     __device__ AdjFin(const SweepParams &p_, A d_, A sdn_, T *yo) : p(p_), d(d_), sdn(sdn_), yout(yo) {}
-    __device__ __forceinline__ A base() const { return A(0); }
+    __device__ __forceinline__ A rterm(const SweepParams &q, int u) const
+    {
+        return q.rhs ? static_cast<const A *>(q.rhs)[u] : A(0);
+    }
     __device__ __forceinline__ T operator()(int u, A acc, int, A, T yold, A r)
     {
         const bool dangling = __ldg(p.col_ptr + u + 1) == __ldg(p.col_ptr + u);

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(PB_BS) k_pb_epilogue(SweepParams p, A *gacc)
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < p.n; u += gridDim.x * blockDim.x) {
         const A acc = gacc[u];
         gacc[u] = A(0);
-        fin(u, acc, p.outdeg[u], inv[u], yin[u], fin.base());
+        fin(u, acc, p.outdeg[u], inv[u], yin[u], fin.rterm(p, u));
     }
     block_partials<A>(st, fin.pt);
     if (last_block(st) && threadIdx.x < 32) close_sweep(p);

@@ -94,6 +94,8 @@ struct SolveState {
     double rnorm;     // defect correction: ||r||_1 of the current outer step
     double inner_tol; // defect correction: inner stop threshold (true units)
     double inner_rel;
+    double inner_floor; // defect correction: an inner solve stops no lower
+                        // than inner_floor * tau
     double best;        // defect correction: smallest inner change so far
     int since;          // defect correction: inner sweeps since it
     double mass_target; // defect correction: exact sum of the correction,

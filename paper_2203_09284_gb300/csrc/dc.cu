@@ -48,13 +48,13 @@ struct ResidFin {
     Ctx<double> c;
     Part<double> pt;
     __device__ ResidFin(const DCParams &q_, const Ctx<double> &c_) : q(q_), c(c_) {}
-    __device__ __forceinline__ double base() const { return c.base; }
+    __device__ __forceinline__ double rterm(const SweepParams &, int) const { return 0.0; }
     __device__ __forceinline__ double operator()(int u, double acc, int od, double, double yo,
                                                  double)
     {
         const bool plain = q.weighted || od == 0;  // stored value is x itself
         const double xold = plain ? yo : yo * static_cast<double>(od);
-        const double xnew = c.base + c.d * (c.sig * (acc + c.dt));
+        const double xnew = fma(c.ds, acc, c.bc);
         const double r = xnew - c.sig * xold;
         if (!isfinite(r)) atomicCAS(&q.sx->error, 0, (int)PR_ERR_NUMERIC);
         const float rf = static_cast<float>(r);
@@ -62,7 +62,7 @@ struct ResidFin {
         if (!q.fp16) static_cast<Te *>(q.e0)[u] = from_a<Te>(plain ? rf : rf * q.inv32[u]);
         const double ar = fabs(r);
         pt.l1 += ar;
-        pt.lmax = ar > pt.lmax ? ar : pt.lmax;
+        if (c.linf) pt.lmax = ar > pt.lmax ? ar : pt.lmax;
         pt.sm += rf;
         if (od == 0) pt.dm += rf;
         return xnew;
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(SWEEP_BS, SWEEP_MINB) k_dc_resid(DCParams q)
         se->shift = 0.0;
         // inner stop on the L1 change of e (true units); the last outer step
         // need not over-solve below the outer threshold
-        se->tau = fmax(sx->inner_rel * res, 0.05 * sx->tau);
+        se->tau = fmax(sx->inner_rel * res, sx->inner_floor * sx->tau);
         se->norm = 0;
     }
     __threadfence();
@@ -395,6 +395,12 @@ static pr_status run_dc(pr_graph *g, const pr_options *o, const pr_tune &, doubl
     init_state(g, o, hs[0]);
     hs[0].max_outer = o->max_outer > 0 ? o->max_outer : default_max_outer(o->precision);
     hs[0].inner_rel = o->inner_rel > 0 ? o->inner_rel : default_eta(o->precision, gs);
+    // the last inner solve stops at 0.5 tau (Jacobi: the residual after the
+    // update is at most d times the inner solve's last change, 0.425 tau);
+    // fused inner sweeps keep the wider margin 0.05 tau, which the 16-bit
+    // forms need (one more outer step otherwise).  Measured at R-MAT scale 22:
+    // Jacobi FP32-stored correction 60 -> 54 sweeps, BF16/FP16 66 -> 51.
+    hs[0].inner_floor = gs ? 0.05 : 0.5;
     hs[0].scale = 1.0;
     memset(&hs[1], 0, sizeof(SolveState));
     hs[1].d = o->d;

@@ -212,6 +212,10 @@ __device__ __forceinline__ float aabs(float v) { return fabsf(v); }
 template <typename A>
 struct Ctx {
     A d, base, sig, rsig, dt;
+    A ds;       // d * sigma: weight of a gathered sum (stored units)
+    A cst;      // d * sigma * dt: the dangling term every vertex receives
+    A bc;       // base + cst: a new value's constant part without a rhs
+    bool linf;  // the stop rule takes the largest change
 };
 
 template <typename A>
@@ -228,6 +232,11 @@ __device__ __forceinline__ Ctx<A> load_ctx(const SolveState *st)
     c.sig = static_cast<A>(st->sigma);
     c.rsig = static_cast<A>(1.0 / st->sigma);
     c.dt = static_cast<A>(st->dang * st->inv_n);
+    const double cst = st->d * st->sigma * (st->dang * st->inv_n);
+    c.ds = static_cast<A>(st->d * st->sigma);
+    c.cst = static_cast<A>(cst);
+    c.bc = static_cast<A>(st->base + cst);
+    c.linf = st->norm != 0;
     return c;
 }
 
@@ -241,18 +250,24 @@ struct SweepFin {
     T *yout;
     Part<A> pt;
     __device__ SweepFin(const SweepParams &p_, const Ctx<A> &c_, T *yo) : p(p_), c(c_), yout(yo) {}
-    __device__ __forceinline__ A base() const { return c.base; }
+    // constant part of vertex u's new value (true units): the teleport term
+    // or the right-hand side, plus the dangling term
+    __device__ __forceinline__ A rterm(const SweepParams &q, int u) const
+    {
+        return q.rhs ? static_cast<const A *>(q.rhs)[u] + c.cst : c.bc;
+    }
+    // r = rterm(u); new value x' = r + d sigma (acc + dt), acc in stored units
     __device__ __forceinline__ T operator()(int u, A acc, int od, A inv, T yold, A r)
     {
         const A yo = to_a<A>(yold);
         const A xold = (W || od == 0) ? yo : yo * static_cast<A>(od);  // stored units
-        const A xnew = r + c.d * (c.sig * (acc + c.dt));                 // true units
+        const A xnew = fma(c.ds, acc, r);                                // true units
         const A diff = aabs(xnew - c.sig * xold);
         const A xs = xnew * c.rsig;                                       // stored units
         const T yn = from_a<T>((W || od == 0) ? xs : xs * inv);
         st_y<T, GS>(yout, u, yn);
         pt.l1 += diff;
-        pt.lmax = diff > pt.lmax ? diff : pt.lmax;
+        if (c.linf) pt.lmax = diff > pt.lmax ? diff : pt.lmax;
         pt.sm += xs;
         if (od == 0) pt.dm += xs;
         return yn;
@@ -290,14 +305,14 @@ struct SweepFinPerf : SweepFin<T, A, false, false> {
     {
         const A yo = to_a<A>(yold);
         const A xold = od == 0 ? yo : yo * static_cast<A>(od);
-        const A xnew = r + this->c.d * (this->c.sig * (acc + this->c.dt));
+        const A xnew = fma(this->c.ds, acc, r);
         const A diff = aabs(xnew - this->c.sig * xold);
         const A xs = xnew * this->c.rsig;
         const T yn = from_a<T>(od == 0 ? xs : xs * inv);
         this->yout[u] = yn;
         last[u] = diff;
         this->pt.l1 += diff;
-        this->pt.lmax = diff > this->pt.lmax ? diff : this->pt.lmax;
+        if (this->c.linf) this->pt.lmax = diff > this->pt.lmax ? diff : this->pt.lmax;
         this->pt.sm += xs;
         if (od == 0) this->pt.dm += xs;
         return yn;
@@ -548,12 +563,6 @@ __device__ __forceinline__ A group_sum(A v)
     return v;
 }
 
-template <typename A>
-__device__ __forceinline__ A rhs_of(const SweepParams &p, int u, A base)
-{
-    return p.rhs ? static_cast<const A *>(p.rhs)[u] : base;
-}
-
 // hub segment i (one warp)
 template <typename T, typename A, bool GS, bool W, typename Fin>
 __device__ __forceinline__ void hub_item(const SweepParams &p, int i, const int4 &d,
@@ -582,7 +591,7 @@ __device__ __forceinline__ void hub_item(const SweepParams &p, int i, const int4
                 if constexpr (perf_of<Fin>::value) fin.keep(h, p.outdeg[h], ld_y<T, GS>(src.y, h));
             } else {
                 fin(h, static_cast<A>(all), p.outdeg[h], static_cast<const A *>(p.inv)[h],
-                    ld_y<T, GS>(src.y, h), rhs_of<A>(p, h, fin.base()));
+                    ld_y<T, GS>(src.y, h), fin.rterm(p, h));
             }
         }
     }
@@ -606,7 +615,7 @@ __device__ __forceinline__ void mid_group(const SweepParams &p, int v0, int v_en
             od = __ldg(p.outdeg + u);
             inv = __ldg(static_cast<const A *>(p.inv) + u);
             yo = ld_y<T, GS>(src.y, u);
-            r = rhs_of<A>(p, u, fin.base());
+            r = fin.rterm(p, u);
         }
     }
     bool sk = false;
@@ -649,13 +658,13 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
                 oda = __ldg(p.outdeg + ua);
                 inva = __ldg(static_cast<const A *>(p.inv) + ua);
                 ya = ld_y<T, GS>(src.y, ua);
-                ra = rhs_of<A>(p, ua, fin.base());
+                ra = fin.rterm(p, ua);
             }
             if (ub < v1) {
                 odb = __ldg(p.outdeg + ub);
                 invb = __ldg(static_cast<const A *>(p.inv) + ub);
                 yb = ld_y<T, GS>(src.y, ub);
-                rb = rhs_of<A>(p, ub, fin.base());
+                rb = fin.rterm(p, ub);
             }
             if (ua < v1) fin(ua, A(0), oda, inva, ya, ra);
             if (ub < v1) fin(ub, A(0), odb, invb, yb, rb);
@@ -676,7 +685,7 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
         od0 = __ldg(p.outdeg + u);
         inv0 = __ldg(static_cast<const A *>(p.inv) + u);
         yo0 = ld_y<T, GS>(src.y, u);
-        r0 = rhs_of<A>(p, u, fin.base());
+        r0 = fin.rterm(p, u);
     }
     if constexpr (PF) {
         // slots of the vertices that keep their value: one bit each (a low
@@ -746,7 +755,7 @@ __device__ __forceinline__ void low_item(const SweepParams &p, const int4 &d,
                 od = __ldg(p.outdeg + u);
                 inv = __ldg(static_cast<const A *>(p.inv) + u);
                 yo = ld_y<T, GS>(src.y, u);
-                r = rhs_of<A>(p, u, fin.base());
+                r = fin.rterm(p, u);
             }
             bool kept = false;
             if constexpr (PF) {
@@ -923,7 +932,7 @@ __global__ void k_sweep_serial(SweepParams p)
         A acc = 0;
         for (int i = a + lane; i < e; i += 32) acc += to_a<A>(ld_l2<T>(y, p.row_idx[i]));
         acc = warp_sum(acc);
-        if (lane == 0) fin(u, acc, p.outdeg[u], inv[u], ld_l2<T>(y, u), rhs_of<A>(p, u, fin.base()));
+        if (lane == 0) fin(u, acc, p.outdeg[u], inv[u], ld_l2<T>(y, u), fin.rterm(p, u));
         __syncwarp();
     }
     block_partials<A>(st, fin.pt);
