@@ -42,9 +42,9 @@ METRIC = "R-MAT-22 time to L1<1e-10 and GTEPS (% HBM peak), mixed/fused vs plain
 # summarised in profiles/ (see the commands there); reported only while the
 # sweep's sources are the ones captured.
 SWEEP_TRAFFIC = {
-    "sources_sha256": "319d1a615b5ca039f7cb6db8cda5e377d5849a72e316872d8e16794662c66387",
-    "fp32": 341392896,  # 337,219,584 read + 4,173,312 written
-    "fp64": 393987328,  # 376,306,944 read + 17,680,384 written
+    "sources_sha256": "03717ae1bac18ed639395562584a3d41eb38ad535bc824ab814a951a461c4078",
+    "fp32": 335180544,  # 331,412,480 read + 3,768,064 written
+    "fp64": 385481472,  # 369,688,320 read + 15,793,152 written
 }
 SWEEP_SOURCES = ("sweep.cuh", "tma.cuh", "common.cuh")
 
