@@ -270,9 +270,10 @@ __global__ void k_run_degrees(int64_t m, const uint64_t *__restrict__ keys, int 
 // of them in digit-major order (the output start of each (digit, tile)),
 // then the scatter: persistent blocks take tiles round-robin; a block ranks
 // its tile by digit (stable: warp w ranks the w-th 512-pair run in 16 rounds
-// of 32 with __match_any_sync), reorders it by digit in shared memory and
-// writes each digit's run to its place, while the bulk copy (TMA) of its
-// next tile lands in shared memory.  Every copy wait is bounded.
+// of 32, a lane's peers found with one ballot per digit bit), reorders it by
+// digit in shared memory and writes each digit's run to its place, while
+// the bulk copy (TMA) of its next tile lands in shared memory.  Every copy
+// wait is bounded.
 constexpr int RS_BS = 256;
 constexpr int RS_ROUNDS = 16;
 constexpr int RS_TILE = RS_BS * RS_ROUNDS;
@@ -283,7 +284,7 @@ constexpr uint32_t RS_WAIT_LIMIT = 1u << 22;
 // Digit counts of tile blockIdx.x: all 16 keys of a thread are loaded
 // (streaming, read once) before the shared-memory increments.
 __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t m, int shift,
-                             int32_t *counts, int64_t ntiles)
+                             int32_t *counts, int64_t ntiles, unsigned *used)
 {
     __shared__ int hist[256];
     hist[threadIdx.x] = 0;
@@ -299,7 +300,13 @@ __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int64_t m, int s
     for (int j = 0; j < RS_ROUNDS; ++j)
         if (dg[j] >= 0) atomicAdd(&hist[dg[j]], 1);
     __syncthreads();
-    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = hist[threadIdx.x];
+    const int c = hist[threadIdx.x];
+    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = c;
+    // OR of the digits present (the scatter picks its ranking method by it);
+    // an atomic only where it adds a bit, so the word does not serialise
+    // every block
+    const unsigned o = __reduce_or_sync(FULL, c ? (unsigned)threadIdx.x : 0u);
+    if ((threadIdx.x & 31) == 0 && (o & ~__ldcg(used))) atomicOr(used, o);
 }
 
 struct RadixSmem {
@@ -318,12 +325,13 @@ struct RadixSmem {
 __global__ void __launch_bounds__(RS_BS, RS_BLOCKS_PER_SM) k_radix_scatter(
     const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     int32_t *__restrict__ vout, int64_t m, int shift, const int32_t *__restrict__ offsets,
-    int32_t *err)
+    int32_t *err, const unsigned *used)
 {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     RadixSmem &sm = *reinterpret_cast<RadixSmem *>(rs_smem);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    const bool few = *used < 64u;  // every digit of this pass below 64
     const int64_t ntiles = (m + RS_TILE - 1) / RS_TILE;
     auto is_full = [&](int64_t t) { return t < ntiles && (t + 1) * RS_TILE <= m; };
     // a full tile arrives by bulk copy (16-byte aligned, 48 KB), the last
@@ -382,11 +390,26 @@ __global__ void __launch_bounds__(RS_BS, RS_BLOCKS_PER_SM) k_radix_scatter(
         for (int j = 0; j < RS_ROUNDS; ++j) {
             const bool valid = warp * (RS_ROUNDS * 32) + j * 32 + lane < nvalid;
             const int dg = (int)((k[j] >> shift) & 0xFF);
+            // the valid lanes with this lane's digit: with at most 64
+            // digits present in the pass, match.any; else one ballot per
+            // digit bit (match.any kept the SM's address-divergence unit 80%
+            // busy on full 8-bit digits and bound the pass; it is the faster
+            // of the two when most lanes share few digits)
             const unsigned vmask = __ballot_sync(FULL, valid);
+            unsigned peers;
+            if (few) {
+                peers = valid ? __match_any_sync(vmask, dg) : 0u;
+            } else {
+                peers = vmask;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const bool bit = (dg >> b) & 1;
+                    const unsigned mb = __ballot_sync(FULL, bit);
+                    peers &= bit ? mb : ~mb;
+                }
+            }
             int before = 0, r = 0;
-            unsigned peers = 0;
             if (valid) {
-                peers = __match_any_sync(vmask, dg);
                 r = __popc(peers & lt);
                 before = sm.wcnt[warp][dg];
             }
@@ -448,13 +471,15 @@ pr_status radix_sort(pr_graph *g, uint64_t *keys, int32_t *vals, uint64_t *alt_k
     }
     const int64_t ntiles = (m + RS_TILE - 1) / RS_TILE;
     const int64_t ncount = 256 * ntiles;
-    // scratch: counts [256][ntiles] (+ total), error word
+    // scratch: counts [256][ntiles] (+ total), error word, one word per pass
+    // for the OR of the digits present
     Buf scratch;
-    PR_TRY(buf_alloc(g, scratch, sizeof(int32_t) * (size_t)(ncount + 2), s));
+    PR_TRY(buf_alloc(g, scratch, sizeof(int32_t) * (size_t)(ncount + 2 + shifts.size()), s));
     int32_t *counts = scratch.as<int32_t>();
     int32_t *err = counts + ncount + 1;
+    unsigned *used = reinterpret_cast<unsigned *>(counts + ncount + 2);
     pr_status st = PR_OK;
-    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t), s);
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int32_t) * (1 + shifts.size()), s);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_radix_scatter),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -463,12 +488,13 @@ pr_status radix_sort(pr_graph *g, uint64_t *keys, int32_t *vals, uint64_t *alt_k
     int32_t *va = vals, *vb = alt_v;
     const unsigned grid = (unsigned)std::min<int64_t>(ntiles, (int64_t)g->num_sms * RS_BLOCKS_PER_SM);
     for (size_t p = 0; p < shifts.size() && e == cudaSuccess && st == PR_OK; ++p) {
-        k_radix_hist<<<(unsigned)ntiles, RS_BS, 0, s>>>(ka, m, shifts[p], counts, ntiles);
+        k_radix_hist<<<(unsigned)ntiles, RS_BS, 0, s>>>(ka, m, shifts[p], counts, ntiles,
+                                                        used + p);
         note_launch();
         st = scan_exclusive(g, counts, counts, ncount, s);
         if (st != PR_OK) break;
         k_radix_scatter<<<grid, RS_BS, sizeof(RadixSmem), s>>>(ka, va, kb, vb, m, shifts[p],
-                                                             counts, err);
+                                                             counts, err, used + p);
         note_launch();
         std::swap(ka, kb);
         std::swap(va, vb);
