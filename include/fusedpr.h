@@ -77,7 +77,10 @@ typedef enum { PR_NORM_L1 = 0, PR_NORM_LINF = 1 } pr_norm;
 /* Device allocator hooks (e.g. a framework's caching allocator).  alloc
  * returns a device pointer of at least `bytes` usable on `stream`, or NULL;
  * free releases it.  When the pr_allocator pointer passed to
- * pr_graph_create is NULL the library uses cudaMallocAsync/cudaFreeAsync. */
+ * pr_graph_create is NULL the library allocates stream-ordered from its own
+ * memory pool of the device (cudaMallocFromPoolAsync/cudaFreeAsync), which
+ * keeps freed memory for later builds and solves until the process exits,
+ * like a caching allocator. */
 typedef struct {
     void *(*alloc)(size_t bytes, void *stream, void *ctx);
     void (*free)(void *ptr, size_t bytes, void *stream, void *ctx);
@@ -213,7 +216,7 @@ pr_status pr_options_default(pr_options *o);
  *           kept, csc_eid/csr_eid still give input positions, weights of
  *           dropped edges are ignored and their pr_backward gradient is 0.
  *           Without it repeated edges count with multiplicity.
- *   alloc   allocator hooks or NULL (cudaMallocAsync); kept by the graph.
+ *   alloc   allocator hooks or NULL (the library's pool); kept by the graph.
  *   out     receives the handle (NULL on error).
  */
 #define PR_BUILD_CSR 1u

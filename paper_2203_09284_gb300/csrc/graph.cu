@@ -478,7 +478,7 @@ static void destroy_impl(pr_graph *g)
     if (!g) return;
     cudaStream_t s = g->mem.stream;
     cudaStreamSynchronize(s);
-    destroy_impl(g->rev);
+    pr_graph_destroy(g->rev);  // built by pr_graph_create (adjoint)
     g->rev = nullptr;
     release_graphs(g);
     for (Buf *b : g->owned) buf_free(g, *b, s);
@@ -826,7 +826,7 @@ extern "C" pr_status pr_graph_create(int32_t n, int64_t m, const int32_t *src, c
     if (e != cudaSuccess) st = cuda_status(e, "device query", __FILE__, __LINE__);
     if (st == PR_OK) st = build_all(g, src, dst, w, flags, s);
     if (st != PR_OK) {
-        destroy_impl(g);
+        pr_graph_destroy(g);
         return st;
     }
     *out = g;

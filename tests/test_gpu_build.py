@@ -202,3 +202,26 @@ def test_build_dedup_weighted():
     assert float(np.abs(x1.cpu().numpy() - star.x).sum()) <= 0.85 / 0.15 * 1e-13 * 1.01
     g.close()
     g2.close()
+
+
+def test_build_without_allocator_hooks_uses_the_library_pool():
+    """A graph created with no allocator hooks takes its memory from the
+    library's own pool; built and solved twice in a row (the second build
+    reuses the memory the first one freed), it matches the graph built
+    through torch's caching allocator exactly."""
+    import paper_2203_09284_gb300 as fp
+    n, src, dst = gen.rmat(12, 8, seed=9, dangling_frac=0.1)
+    ref = graph(n, src, dst)
+    xr, rr = ref.solve(threshold=1e-10)
+    ea = ref.export()
+    for _ in range(2):
+        g = graph(n, src, dst, use_torch_allocator=False)
+        eb = g.export()
+        for k in ea:
+            assert torch.equal(ea[k], eb[k]), k
+        x, r = g.solve(threshold=1e-10)
+        assert r.iters == rr.iters and torch.equal(x, xr)
+        xg, rg = g.solve(variant="gs", precision="fp32_dc", threshold=1e-10)
+        assert rg.status == 0
+        g.close()
+    ref.close()
