@@ -18,6 +18,9 @@
 //
 // Layout: X rows of Bp = 32, 64, 128 or 256 elements (B is padded; wider
 // batches run as several passes of at most 256 FP32 or 128 FP64 columns).
+// A pass whose running columns have fallen to Bp/2 + Bp/8 hands them on to
+// narrower passes (Bp/2 and 32 columns), since a sweep costs what its row
+// width does.
 // One warp owns a vertex row: lane l holds the columns l*w + k of every
 // 32*w-wide chunk (w = elements per 16-byte access), so each gathered row is
 // one contiguous, fully used read of 128 to 1024 bytes.  Rows are gathered
@@ -49,6 +52,7 @@ struct BatchState {
     int error;
     int ncols;  // real columns of this pass
     double tau, d;
+    int paused;  // the loop ended early to split the pass (done is set too)
 };
 
 struct BatchParams {
@@ -76,6 +80,8 @@ struct BatchParams {
     int32_t stall;            // stop columns at their rounding floor (FP32)
     const void *tele_rows;    // E[n][Bp] dense teleport rows (degree-ordered ids)
                               // or null: one-hot seeds
+    int32_t pause_at;         // end the loop early (paused) once at most this
+                              // many columns are still running (-1: never)
     BatchState *st;
     cudaGraphConditionalHandle cond;
     int32_t use_cond;
@@ -359,9 +365,13 @@ __global__ void __launch_bounds__(BATCH_BS, 1) k_batch_sweep(BatchParams p)
         st->ticket = 0;
         st->iter = iter + 1;
         const bool stop = n_active == 0 || iter + 1 >= st->max_iter;
-        st->done = stop ? 1 : 0;
+        // enough columns stopped: end the loop so the host moves the running
+        // ones into narrower passes
+        const bool pause = !stop && n_active <= p.pause_at;
+        st->done = (stop || pause) ? 1 : 0;
+        st->paused = pause ? 1 : 0;
         __threadfence();
-        if (p.use_cond) cudaGraphSetConditional(p.cond, stop ? 0u : 1u);
+        if (p.use_cond) cudaGraphSetConditional(p.cond, (stop || pause) ? 0u : 1u);
     }
 }
 
@@ -429,19 +439,22 @@ __global__ void k_batch_init(BatchParams p, const int32_t *__restrict__ seeds,
 }
 
 // Dense teleport rows of the pass in the degree-ordered ids:
-// out[k][b] = V[n2o[k]][c0 + b] for the pass's columns, 0 in the padding;
-// flag 2 in *bad for a negative or non-finite entry.
+// out[k][b] = V[n2o[k]][c0 + cols[b]] for the pass's row positions b (cols
+// null: cols[b] = b for b < ncols; a negative column: padding, 0); flag 2
+// in *bad for a negative or non-finite entry.
 template <typename E, int BP>
 __global__ void k_batch_tele(int32_t n, const E *__restrict__ V, int ld, int c0, int ncols,
-                             const int32_t *__restrict__ n2o, E *out, int32_t *bad)
+                             const int32_t *__restrict__ n2o, E *out, int32_t *bad,
+                             const int32_t *__restrict__ cols)
 {
     const size_t total = (size_t)n * BP;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(i / BP), b = (int)(i % BP);
+        const int col = cols ? cols[b] : (b < ncols ? b : -1);
         E v = E(0);
-        if (b < ncols) {
-            v = V[(size_t)n2o[k] * ld + c0 + b];
+        if (col >= 0) {
+            v = V[(size_t)n2o[k] * ld + c0 + col];
             if (!(v >= E(0)) || isinf((double)v)) atomicOr(bad, 2);
         }
         out[i] = v;
@@ -476,17 +489,36 @@ __global__ void __launch_bounds__(BATCH_BS, 1) k_batch_colsum(BatchParams p, con
     }
 }
 
-// X_out[u][c0 + b] = x[o2n[u]][b] / sum_b for the pass's real columns.
+// X_out[u][c0 + outmap[b]] = x[o2n[u]][b] / sum_b for the row positions b
+// with outmap[b] >= 0 (the columns written now).
 template <typename E, int BP>
 __global__ void k_batch_out(BatchParams p, const E *x, const int32_t *__restrict__ o2n,
-                            int ncols, int ld, int c0, E *X_out)
+                            const int32_t *__restrict__ outmap, int ld, int c0, E *X_out)
 {
-    const size_t total = (size_t)p.n * ncols;
+    const size_t total = (size_t)p.n * BP;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (size_t)gridDim.x * blockDim.x) {
-        const int u = (int)(i / ncols), b = (int)(i % ncols);
+        const int u = (int)(i / BP), b = (int)(i % BP);
+        const int col = outmap[b];
+        if (col < 0) continue;
         const double sum = fx_value(p.acc[4 * b], p.acc[4 * b + 1]);
-        X_out[(size_t)u * ld + c0 + b] = (E)((double)x[(size_t)o2n[u] * BP + b] / sum);
+        X_out[(size_t)u * ld + c0 + col] = (E)((double)x[(size_t)o2n[u] * BP + b] / sum);
+    }
+}
+
+// A narrower pass's first iterate from its parent's rows: y[u][i] =
+// x[u][from[i]] (x rows of bp_src entries; from[i] < 0: padding, 0).
+template <typename E, int BP>
+__global__ void k_batch_take(int32_t n, const E *__restrict__ x, int bp_src,
+                             const int32_t *__restrict__ from, E *y)
+{
+    const size_t total = (size_t)n * BP;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const size_t u = i / BP;
+        const int b = (int)(i % BP);
+        const int f = from[b];
+        y[i] = f >= 0 ? x[u * (size_t)bp_src + f] : E(0);
     }
 }
 
@@ -533,12 +565,38 @@ static pr_status ensure_batch_items(pr_graph *g, cudaStream_t s)
 }
 
 // Per-column state in one buffer: acc [Bp][4] int64, dang/err/best [Bp]
-// double, conv/seed/since [Bp] int32, then the BatchState.
-static size_t cols_bytes() { return (size_t)BATCH_COLS * (32 + 3 * 8 + 3 * 4) + 256; }
+// double, conv/seed/since [Bp] int32, then the BatchState (and the error
+// word), then two [Bp] int32 maps of row positions to columns.
+constexpr size_t COLS_STATE = (size_t)BATCH_COLS * (32 + 3 * 8 + 3 * 4);
+constexpr size_t COLS_MAPS = COLS_STATE + 256;
+static size_t cols_bytes() { return COLS_MAPS + 2 * sizeof(int32_t) * BATCH_COLS; }
 
+// The state a narrower pass starts from: the columns still running when its
+// parent pass paused, their rows in the parent's iterate and their
+// per-column sums and counters.
+struct BatchResume {
+    int iter;                      // sweeps done
+    const void *x;                 // parent iterate, rows of bp_src entries
+    int bp_src;
+    void *x0, *x1;                 // this pass's iterates (each n x Bp)
+    int count;                     // columns taken over
+    int32_t from[BATCH_COLS];      // their positions in the parent's rows
+    int32_t cols[BATCH_COLS];      // their columns (c0 + cols[i] in X_out)
+    int32_t seed[BATCH_COLS], since[BATCH_COLS];
+    double dang[BATCH_COLS], err[BATCH_COLS], best[BATCH_COLS];
+};
+
+// One pass over up to Bp = 32 * VEC columns: from the start (rs null) or
+// from a parent pass's state.  Once few enough columns are still running
+// (at most Bp/2 + Bp/8), the loop pauses: the stopped columns are written
+// out and the running ones go on in narrower passes (Bp/2 wide, and 32 wide
+// for the rest), which gather half the row bytes or less per in-edge (the
+// batched sweep's time follows its row width; a column's arithmetic does
+// not depend on the pass it is in, so its result is the same).
 template <typename E, int VEC>
 static pr_status batch_pass(pr_graph *g, const pr_options *o, const int32_t *seeds, const E *V,
-                            int ncols, int ld, int c0, E *X_out, pr_result *res, cudaStream_t s)
+                            int ncols, int ld, int c0, E *X_out, pr_result *res, cudaStream_t s,
+                            const BatchResume *rs = nullptr)
 {
     constexpr int BP = 32 * VEC;
     constexpr bool fp64 = sizeof(E) == 8;
@@ -558,9 +616,10 @@ static pr_status batch_pass(pr_graph *g, const pr_options *o, const int32_t *see
     p.seg_start = g->bseg_start.as<int32_t>();
     p.seg_cnt = g->bseg_cnt.as<int32_t>();
     p.part = g->bpart.p;
-    p.x0 = g->bx0.p;
-    p.x1 = g->bx1.p;
+    p.x0 = rs ? rs->x0 : g->bx0.p;
+    p.x1 = rs ? rs->x1 : g->bx1.p;
     p.stall = fp64 ? 0 : 1;
+    p.pause_at = VEC > 1 ? BP / 2 + BP / 8 : -1;
     char *cb = static_cast<char *>(g->bcols.p);
     p.acc = reinterpret_cast<long long *>(cb);
     p.dang = reinterpret_cast<double *>(cb + BATCH_COLS * 32);
@@ -570,25 +629,63 @@ static pr_status batch_pass(pr_graph *g, const pr_options *o, const int32_t *see
     p.seed = p.conv + BATCH_COLS;
     p.since = p.seed + BATCH_COLS;
     p.st = reinterpret_cast<BatchState *>(cb + BATCH_COLS * 68);
+    int32_t *d_map = reinterpret_cast<int32_t *>(cb + COLS_MAPS);   // [Bp]
+    int32_t *d_map2 = d_map + BATCH_COLS;                            // [Bp]
+
+    // row position b holds column cols[b] of the pass (-1: padding)
+    int32_t cols[BATCH_COLS];
+    for (int b = 0; b < BP; ++b) cols[b] = rs ? (b < rs->count ? rs->cols[b] : -1) : (b < ncols ? b : -1);
 
     BatchState hs;
     memset(&hs, 0, sizeof(hs));
     hs.max_iter = o->max_iter;
     hs.tau = o->threshold;
     hs.d = o->d;
-    hs.ncols = ncols;
+    hs.ncols = rs ? rs->count : ncols;
+    hs.iter = rs ? rs->iter : 0;
     PR_CUDA(cudaMemcpyAsync(p.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
     int32_t *bad = reinterpret_cast<int32_t *>(p.st + 1);
     PR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
-    const double dang0 = (double)g->n_dangling * (double)(E)(1.0 / (double)n);
     const int ib = std::max(1, std::min<int>((int)(((size_t)n * BP + 255) / 256), g->num_sms * 8));
-    k_batch_init<E, BP><<<ib, 256, 0, s>>>(p, seeds ? seeds + c0 : nullptr, g->o2n.as<int32_t>(),
-                                           ncols, dang0, bad);
-    note_launch();
+    if (!rs) {
+        const double dang0 = (double)g->n_dangling * (double)(E)(1.0 / (double)n);
+        k_batch_init<E, BP><<<ib, 256, 0, s>>>(p, seeds ? seeds + c0 : nullptr,
+                                               g->o2n.as<int32_t>(), ncols, dang0, bad);
+        note_launch();
+    } else {
+        int32_t conv[BATCH_COLS], seed[BATCH_COLS], since[BATCH_COLS];
+        double dang[BATCH_COLS], err[BATCH_COLS], best[BATCH_COLS];
+        int32_t from[BATCH_COLS];
+        for (int b = 0; b < BP; ++b) {
+            const bool real = b < rs->count;
+            from[b] = real ? rs->from[b] : -1;
+            conv[b] = real ? 0 : -1;
+            seed[b] = real ? rs->seed[b] : -1;
+            since[b] = real ? rs->since[b] : 0;
+            dang[b] = real ? rs->dang[b] : 0.0;
+            err[b] = real ? rs->err[b] : 0.0;
+            best[b] = real ? rs->best[b] : INFINITY;
+        }
+        PR_CUDA(cudaMemcpyAsync(d_map2, from, sizeof(int32_t) * BP, cudaMemcpyHostToDevice, s));
+        k_batch_take<E, BP><<<ib, 256, 0, s>>>(n, static_cast<const E *>(rs->x), rs->bp_src,
+                                               d_map2, static_cast<E *>(p.x0));
+        note_launch();
+        PR_CUDA(cudaMemcpyAsync(p.conv, conv, sizeof(int32_t) * BP, cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaMemcpyAsync(p.seed, seed, sizeof(int32_t) * BP, cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaMemcpyAsync(p.since, since, sizeof(int32_t) * BP, cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaMemcpyAsync(p.dang, dang, sizeof(double) * BP, cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaMemcpyAsync(p.err, err, sizeof(double) * BP, cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaMemcpyAsync(p.best, best, sizeof(double) * BP, cudaMemcpyHostToDevice, s));
+        PR_CUDA(cudaMemsetAsync(p.acc, 0, sizeof(long long) * 4 * BP, s));
+        // the first sweep reads x0: an even sweep count here, else swap
+        if (hs.iter & 1) std::swap(p.x0, p.x1);
+        PR_CUDA(cudaStreamSynchronize(s));  // the host arrays above go out of scope
+    }
     if (V) {
         PR_TRY(buf_alloc(g, g->btele, (size_t)n * BP * sizeof(E), s));
+        PR_CUDA(cudaMemcpyAsync(d_map, cols, sizeof(int32_t) * BP, cudaMemcpyHostToDevice, s));
         k_batch_tele<E, BP><<<ib, 256, 0, s>>>(n, V, ld, c0, ncols, g->n2o.as<int32_t>(),
-                                               g->btele.as<E>(), bad);
+                                               g->btele.as<E>(), bad, d_map);
         note_launch();
         p.tele_rows = g->btele.p;
     }
@@ -609,6 +706,7 @@ static pr_status batch_pass(pr_graph *g, const pr_options *o, const int32_t *see
     const int nitems = p.nseg + (n - p.nhub);
     const unsigned grid =
         (unsigned)std::max(1, std::min((nitems + BATCH_WARPS - 1) / BATCH_WARPS, g->num_sms));
+    const int iter0 = hs.iter;
     if (o->use_graph) {
         cudaGraph_t graph = nullptr;
         PR_CUDA(cudaGraphCreate(&graph, 0));
@@ -642,35 +740,32 @@ static pr_status batch_pass(pr_graph *g, const pr_options *o, const int32_t *see
         if (e != cudaSuccess) return cuda_status(e, "batched loop graph", __FILE__, __LINE__);
         PR_CUDA(cudaMemcpyAsync(&hs, p.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
         PR_CUDA(cudaStreamSynchronize(s));
-        note_launch((uint64_t)hs.iter + 1);
+        note_launch((uint64_t)(hs.iter - iter0) + 1);
     } else {
         p.use_cond = 0;
         void *args[] = {&p};
-        int launched = 0;
-        while (launched < o->max_iter) {
-            const int batch = std::min(16, o->max_iter - launched);
+        while (hs.iter < o->max_iter) {
+            const int batch = std::min(16, o->max_iter - hs.iter);
             for (int k = 0; k < batch; ++k) {
                 PR_CUDA(cudaLaunchKernel(func, dim3(grid), dim3(BATCH_BS), args, smem, s));
                 note_launch();
             }
-            launched += batch;
             PR_CUDA(cudaMemcpyAsync(&hs, p.st, sizeof(hs), cudaMemcpyDeviceToHost, s));
             PR_CUDA(cudaStreamSynchronize(s));
             if (hs.done) break;
         }
     }
 
-    // column sums, output, per-column results
+    // column sums of the iterate; the stopped columns (all of them at the
+    // end) written out with their results
     const E *xf = static_cast<const E *>((hs.iter & 1) ? p.x1 : p.x0);
+    E *xfree = static_cast<E *>((hs.iter & 1) ? p.x0 : p.x1);
+    const bool split = hs.paused != 0;
     const size_t smem_s = (size_t)BATCH_WARPS * BP * sizeof(double);
     PR_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void *>(&k_batch_colsum<E, VEC>),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s));
     k_batch_colsum<E, VEC><<<g->num_sms, BATCH_BS, smem_s, s>>>(p, xf);
     note_launch();
-    k_batch_out<E, BP><<<g->num_sms * 8, 256, 0, s>>>(p, xf, g->o2n.as<int32_t>(), ncols, ld, c0,
-                                                       X_out);
-    note_launch();
-    PR_LAUNCH_CHECK();
     long long acc[BATCH_COLS * 4];
     double err[BATCH_COLS];
     int32_t conv[BATCH_COLS];
@@ -678,19 +773,102 @@ static pr_status batch_pass(pr_graph *g, const pr_options *o, const int32_t *see
     PR_CUDA(cudaMemcpyAsync(err, p.err, sizeof(double) * BP, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaMemcpyAsync(conv, p.conv, sizeof(int32_t) * BP, cudaMemcpyDeviceToHost, s));
     PR_CUDA(cudaStreamSynchronize(s));
+    int32_t outmap[BATCH_COLS];
+    for (int b = 0; b < BP; ++b) {
+        const bool stopped = conv[b] > 0 || conv[b] <= -2;
+        outmap[b] = (cols[b] >= 0 && (!split || stopped)) ? cols[b] : -1;
+    }
+    PR_CUDA(cudaMemcpyAsync(d_map, outmap, sizeof(int32_t) * BP, cudaMemcpyHostToDevice, s));
+    k_batch_out<E, BP><<<g->num_sms * 8, 256, 0, s>>>(p, xf, g->o2n.as<int32_t>(), d_map, ld, c0,
+                                                       X_out);
+    note_launch();
+    PR_LAUNCH_CHECK();
     pr_status all = PR_OK;
-    for (int b = 0; b < ncols; ++b) {
+    for (int b = 0; b < BP; ++b) {
+        if (outmap[b] < 0) continue;
         const int it = conv[b] > 0 ? conv[b] : conv[b] <= -2 ? -conv[b] - 1 : hs.iter;
         const pr_status cs = conv[b] > 0 ? PR_OK : PR_NOT_CONVERGED;
         if (cs != PR_OK) all = PR_NOT_CONVERGED;
         if (!res) continue;
-        pr_result &r = res[c0 + b];
+        pr_result &r = res[c0 + outmap[b]];
         r.iters = it;
         r.outer_iters = 0;
         r.residual = err[b];
         r.sum_before_norm = (double)acc[4 * b] * 9.094947017729282e-13 +
                             (double)acc[4 * b + 1] * 8.271806125530277e-25;
         r.status = cs;
+    }
+    if constexpr (VEC > 1) {
+        if (split) {
+            // the running columns go on in a pass of Bp/2 columns and, for
+            // those beyond, one of 32; both iterate in the free buffer of this
+            // pass (two halves of n x Bp), reading their start from xf
+            BatchResume *rr = new BatchResume;  // large: not on the stack
+            rr->iter = hs.iter;
+            rr->x = xf;
+            rr->bp_src = BP;
+            PR_CUDA(cudaMemcpyAsync(rr->seed, p.seed, sizeof(int32_t) * BP, cudaMemcpyDeviceToHost, s));
+            PR_CUDA(cudaMemcpyAsync(rr->since, p.since, sizeof(int32_t) * BP, cudaMemcpyDeviceToHost, s));
+            PR_CUDA(cudaMemcpyAsync(rr->dang, p.dang, sizeof(double) * BP, cudaMemcpyDeviceToHost, s));
+            PR_CUDA(cudaMemcpyAsync(rr->best, p.best, sizeof(double) * BP, cudaMemcpyDeviceToHost, s));
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) {
+                delete rr;
+                return cuda_status(e, "batched split", __FILE__, __LINE__);
+            }
+            int run[BATCH_COLS], nrun = 0;
+            for (int b = 0; b < BP; ++b)
+                if (cols[b] >= 0 && conv[b] == 0) run[nrun++] = b;
+            const size_t half = (size_t)n * (BP / 2);
+            pr_status st = PR_OK;
+            for (int first = 0; first < nrun;) {
+                const int width = first == 0 ? BP / 2 : 32;
+                const int cnt = std::min(width, nrun - first);
+                BatchResume &q = *rr;
+                // per-column arrays in the sub-pass's order (from the parent)
+                int32_t seed2[BATCH_COLS], since2[BATCH_COLS];
+                double dang2[BATCH_COLS], best2[BATCH_COLS], err2[BATCH_COLS];
+                int32_t from2[BATCH_COLS], cols2[BATCH_COLS];
+                for (int i = 0; i < cnt; ++i) {
+                    const int b = run[first + i];
+                    from2[i] = b;
+                    cols2[i] = cols[b];
+                    seed2[i] = q.seed[b];
+                    since2[i] = q.since[b];
+                    dang2[i] = q.dang[b];
+                    best2[i] = q.best[b];
+                    err2[i] = err[b];
+                }
+                BatchResume *sub = new BatchResume;
+                sub->iter = hs.iter;
+                sub->x = xf;
+                sub->bp_src = BP;
+                sub->x0 = xfree;
+                sub->x1 = xfree + half;
+                sub->count = cnt;
+                memcpy(sub->from, from2, sizeof(int32_t) * cnt);
+                memcpy(sub->cols, cols2, sizeof(int32_t) * cnt);
+                memcpy(sub->seed, seed2, sizeof(int32_t) * cnt);
+                memcpy(sub->since, since2, sizeof(int32_t) * cnt);
+                memcpy(sub->dang, dang2, sizeof(double) * cnt);
+                memcpy(sub->best, best2, sizeof(double) * cnt);
+                memcpy(sub->err, err2, sizeof(double) * cnt);
+                pr_status ss;
+                if (first == 0)
+                    ss = batch_pass<E, VEC / 2>(g, o, seeds, V, ncols, ld, c0, X_out, res, s, sub);
+                else
+                    ss = batch_pass<E, 1>(g, o, seeds, V, ncols, ld, c0, X_out, res, s, sub);
+                delete sub;
+                if (ss != PR_OK && ss != PR_NOT_CONVERGED) {
+                    st = ss;
+                    break;
+                }
+                if (ss == PR_NOT_CONVERGED) all = PR_NOT_CONVERGED;
+                first += cnt;
+            }
+            delete rr;
+            if (st != PR_OK) return st;
+        }
     }
     return all;
 }

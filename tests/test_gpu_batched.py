@@ -206,3 +206,48 @@ def test_batched_dense_teleport_across_passes(s12, precision, B):
         tol = 1e-12 if precision == "fp64" else FP32_BOUND
         assert l1(Xh[:, b], run.x) <= tol, b
         assert abs(Xh[:, b].sum() - 1) < (1e-13 if precision == "fp64" else 1e-5)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batched_split_keeps_every_column_exact(precision):
+    """72 of the 128 seeds are dangling vertices, whose columns converge far
+    more slowly than the others (about 92 against 16-23 sweeps on this
+    graph).  Once the fast ones have stopped, the 128-column pass writes them
+    out and hands its 72 running columns to a 64-column pass and a 32-column
+    one.  A column's arithmetic does not depend on the pass it is in: every
+    column equals its seed solved alone, bit for bit, with the same sweep
+    count and residual; one-hot teleport vectors in V (handed over with
+    their columns) give the same result; sampled columns match the oracle."""
+    n, src, dst = gen.rmat(12, 8, seed=5)          # about 40% of the vertices dangling
+    og = oracle.build_graph(n, src, dst)
+    g = graph(n, src, dst)
+    outdeg = np.bincount(src, minlength=n)
+    dangling, live = np.flatnonzero(outdeg == 0), np.flatnonzero(outdeg > 0)
+    seeds = np.concatenate([dangling[:72], live[::max(1, len(live) // 56)][:56]]).astype(np.int32)
+    seeds = seeds[np.random.default_rng(3).permutation(len(seeds))]
+    slow = np.isin(seeds, dangling)
+    X, res = g.solve_batched(dev(seeds), threshold=TAU, precision=precision)
+    its = np.array([r.iters for r in res])
+    assert its[~slow].max() * 2 < its[slow].min()   # two groups: the split happens
+    for b in range(len(seeds)):
+        Xb, rb = g.solve_batched(dev(seeds[b:b + 1]), threshold=TAU, precision=precision)
+        assert torch.equal(X[:, b], Xb[:, 0]), b
+        assert res[b].iters == rb[0].iters and res[b].status == rb[0].status, b
+        assert res[b].residual == rb[0].residual, b
+    dt = np.float64 if precision == "fp64" else np.float32
+    onehot = np.zeros((n, len(seeds)), dt)
+    onehot[seeds, np.arange(len(seeds))] = 1
+    Xv, rv = g.solve_batched(V=dev(onehot), threshold=TAU, precision=precision)
+    assert torch.equal(X, Xv)
+    assert [r.iters for r in rv] == list(its)
+    Xh = X.cpu().numpy()
+    for b in range(0, len(seeds), 9):
+        tele = np.zeros(n)
+        tele[seeds[b]] = 1.0
+        run = oracle.jacobi(og, D, tau=TAU, max_iter=1000, tele=tele, dangling_along_tele=True)
+        if precision == "fp64":
+            assert abs(res[b].iters - run.iters) <= 1 and l1(Xh[:, b], run.x) <= 1e-12, b
+        else:
+            star = oracle.fixed_point(og, D, tele=tele, dangling_along_tele=True, max_iter=400)
+            assert l1(Xh[:, b], star.x) <= FP32_BOUND, b
+    g.close()
